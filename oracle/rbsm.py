@@ -1,0 +1,69 @@
+"""ctypes front end of the plain C oracle (test infrastructure).
+
+``evaluate`` follows Listing 1 of the paper with Listings 2-5 for every
+fragment: shadow test (Eq. 1), four-neighbourhood discontinuity (Eqs. 2-4),
+edge traversal (Listing 3), normalisation (Eq. 5) and the optimized
+silhouette (Listing 4) or filtering (Listing 5) visibility.  The readings of
+the paper's undefined helpers are documented in ``rbsm_oracle.c``.
+"""
+import ctypes
+import numpy as np
+
+from . import build as _build
+
+MODE_SILHOUETTE = 1
+MODE_FILTER = 2
+MAXDIST = 16  # §3.1.3: the traversal cap the paper used
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        lib.oracle_rbsm_eval.restype = ctypes.c_int
+        lib.oracle_rbsm_eval.argtypes = [
+            ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+            ctypes.c_int32, ctypes.c_int32,
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def evaluate(depth, x, y, z, mode, max_dist=MAXDIST, want_rd=False, want_nrd=False):
+    """Visibility (float64), codes (uint16) and optionally the four walks and
+    the normalised vector for every fragment.
+
+    depth: 2-D float32 array (height, width), row-major.
+    x, y, z: 1-D float32 arrays of equal length.
+    """
+    lib = _load()
+    depth = np.ascontiguousarray(depth, dtype=np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    z = np.ascontiguousarray(z, dtype=np.float32)
+    n = x.shape[0]
+    if y.shape[0] != n or z.shape[0] != n:
+        raise ValueError("x, y, z must have the same length")
+    h, w = depth.shape
+    vis = np.empty(n, np.float64)
+    codes = np.empty(n, np.uint16)
+    rd = np.empty((n, 4), np.int32) if want_rd else None
+    nrd = np.empty((n, 4), np.float64) if want_nrd else None
+    rc = lib.oracle_rbsm_eval(_ptr(depth), w, h, w, _ptr(x), _ptr(y), _ptr(z), n,
+                              int(mode), int(max_dist), _ptr(vis), _ptr(codes), _ptr(rd), _ptr(nrd))
+    if rc != 0:
+        raise ValueError("oracle_rbsm_eval rejected its arguments (rc=%d)" % rc)
+    out = {"vis": vis, "codes": codes}
+    if want_rd:
+        out["rd"] = rd
+    if want_nrd:
+        out["nrd"] = nrd
+    return out

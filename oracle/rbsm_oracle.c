@@ -1,0 +1,302 @@
+/*
+ * Plain CPU oracle of the per-fragment revectorization-based shadow mapping
+ * (RBSM) path with the optimized visibility functions of Macedo, Apolinario
+ * and Aguero, "Optimized Visibility Functions for Revectorization-Based
+ * Shadow Mapping" (TR-PGCOMP-007/2017).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct judge
+ * of the CUDA path.  Only the tests, the smoke check and the benchmark's CPU
+ * baseline may load it.  It shares no code, header, table or helper with the
+ * CUDA library, and it never reads a value the CUDA library produced.
+ *
+ * Build: gcc -O2 -ffp-contract=off -shared -fPIC (no fast-math).  Contraction
+ * must stay off so that the single-precision silhouette decision below is the
+ * plain IEEE sequence of operations on every host (aarch64 GCC contracts
+ * a*b+c into FMA by default).
+ *
+ * Conventions (the paper's statement of the problem, Listing 1 / §3):
+ *   - the shadow map SM is a width x height array of depths, row-major, row j
+ *     at texture coordinate y in [j/height, (j+1)/height);
+ *   - a fragment p = (x, y, z): x, y texture coordinates in [0,1), z its depth
+ *     as seen from the light;
+ *   - visibility 1 = lit, 0 = shadow (Eq. 1).
+ *
+ * Readings of points the paper leaves open (each is repeated where it acts):
+ *   R1  nearest-texel addressing: i = floor(x*W) with x*W formed in single
+ *       precision (the paper's GLSL float); neighbours are integer i+-1, j+-1.
+ *   R2  texels outside the map are clamped to the edge.
+ *   R3  no depth bias: Eq. 1 exactly (strict '>').
+ *   R4  neighbour order (left, right, +y, -y) as in Listing 2; +y is the
+ *       neighbour at the next row index.
+ *   R5  checkDiscontinuity (used in Listing 3, never printed): the neighbour's
+ *       own four-neighbourhood discontinuity, evaluated with the fragment's
+ *       depth, shares at least one direction with the fragment's (§3.1.3).
+ *   R6  computeFragmentDistanceToSE (Listing 1, never printed): one traversal
+ *       per direction, in the order -x, +x, -y, +y (§3.1.3).
+ *   R7  normalizeFragmentDistanceToSE (Listing 1, never printed): per axis the
+ *       fragment's distance to the end that was found, over the length of the
+ *       aliased edge along that axis (§3.1.4, Fig. 3(c), Eq. 5).
+ *   R8  the end counts of Eq. 5 are raw on both sides of the edge.
+ *   R9  the traversal visits k = 1..MAXDIST texels (Listing 3 loop bound).
+ *   R11 the I-shape test of Listing 5 reads "nrd.w == -1" on its second term
+ *       (the printed "nrd.w == 1" cannot be reached after the U-shape tests).
+ *   R13 a traversal that runs out of steps found no end; its distance is
+ *       -(MAXDIST + 1).
+ *   R15 the equality tests on d and nrd compare exact codes.
+ *   R17 a fragment outside [0,1) is clamped to the edge texel; its in-texel
+ *       offset is still frac(x*W).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <stdlib.h>
+
+#define ORACLE_MODE_SILHOUETTE 1
+#define ORACLE_MODE_FILTER     2
+
+typedef struct {
+    const float *depth;
+    int32_t width, height;
+    int64_t pitch;
+} sm_t;
+
+/* R2: clamp-to-edge fetch of the depth stored in texel (i, j). */
+static float sm_depth(const sm_t *sm, int64_t i, int64_t j)
+{
+    if (i < 0) i = 0;
+    if (i > sm->width - 1) i = sm->width - 1;
+    if (j < 0) j = 0;
+    if (j > sm->height - 1) j = sm->height - 1;
+    return sm->depth[j * sm->pitch + i];
+}
+
+/* Eq. 1 (§3.1.2): s = 0 when the stored blocker is closer to the light than
+ * the fragment (p_z > z(t)), 1 otherwise.  R3: no bias. */
+static int shadow_test(float pz, float zt)
+{
+    if (pz > zt)
+        return 0;
+    return 1;
+}
+
+static int shadow_test_at(const sm_t *sm, int64_t i, int64_t j, float pz)
+{
+    return shadow_test(pz, sm_depth(sm, i, j));
+}
+
+/* Eqs. 2-3 and Listing 2: shadow tests of the four neighbours with the
+ * fragment's depth (R4 order: left, right, +y, -y) and the discontinuity
+ * d_k = |N_k - s|.  Returns s at (i, j); dirs[k] receives d_k. */
+static int discontinuity4(const sm_t *sm, int64_t i, int64_t j, float pz, int dirs[4])
+{
+    int s = shadow_test_at(sm, i, j, pz);
+    int nb[4];
+    nb[0] = shadow_test_at(sm, i - 1, j, pz);
+    nb[1] = shadow_test_at(sm, i + 1, j, pz);
+    nb[2] = shadow_test_at(sm, i, j + 1, pz);
+    nb[3] = shadow_test_at(sm, i, j - 1, pz);
+    for (int k = 0; k < 4; ++k)
+        dirs[k] = nb[k] > s ? nb[k] - s : s - nb[k];
+    return s;
+}
+
+/* Listing 3, §3.1.3 and §3.2.3: walk from texel (i, j) one texel at a time in
+ * direction (di, dj).  The walk ends with +k when the k-th texel has the other
+ * shadow-test result (an end of the shadow edge), with -k when the k-th texel
+ * has the same result but shares no discontinuity direction with the fragment
+ * (R5: it is not part of the same edge), and with -(max_dist + 1) when all
+ * max_dist texels continued (R9, R13). */
+static int traverse_edge(const sm_t *sm, int64_t i, int64_t j, float pz, int s0,
+                         const int dirs0[4], int di, int dj, int max_dist)
+{
+    int64_t ni = i, nj = j;
+    int dist = 1;
+    int found_end = 0;
+    for (int step = 0; step < max_dist; ++step) {
+        ni += di;
+        nj += dj;
+        if (shadow_test_at(sm, ni, nj, pz) != s0) {
+            found_end = 1;
+            break;
+        }
+        int dirs_n[4];
+        (void)discontinuity4(sm, ni, nj, pz, dirs_n);
+        int shared = 0;
+        for (int k = 0; k < 4; ++k)
+            if (dirs_n[k] && dirs0[k])
+                shared = 1;
+        if (!shared)
+            break;
+        dist += 1;
+    }
+    return found_end ? dist : -dist;
+}
+
+/* R7 and Eq. 5: normalisation along one axis.  r_neg / r_pos are the walks
+ * towards decreasing / increasing index, f the in-texel offset of the fragment
+ * along the axis.  The aliased edge along the axis covers |r_neg| + |r_pos| - 1
+ * texels (the fragment's texel plus those each walk passed).  The position is
+ * measured from the side where an end was found, which puts the origin in the
+ * corner of the aliasing (§3.1.4).  code follows Eq. 5: +1 both ends found,
+ * 0 one end, -1 none.  Double-precision variant. */
+static double axis_position_f64(int r_neg, int r_pos, double f, int *code)
+{
+    int len = abs(r_neg) + abs(r_pos) - 1;
+    int ends = (r_neg > 0) + (r_pos > 0);
+    *code = ends == 2 ? 1 : (ends == 1 ? 0 : -1);
+    if (ends == 0)
+        return 1.0;
+    double from_neg = ((double)(r_neg - 1) + f) / (double)len;
+    double from_pos = ((double)(r_pos - 1) + (1.0 - f)) / (double)len;
+    if (ends == 2)
+        return from_neg < from_pos ? from_neg : from_pos;
+    return r_neg > 0 ? from_neg : from_pos;
+}
+
+/* Same normalisation in single precision.  The silhouette visibility turns
+ * this float into a 0/1 decision, so it is taken in the paper's precision
+ * (GLSL float); the operations are one add and one correctly rounded divide. */
+static float axis_position_f32(int r_neg, int r_pos, float f)
+{
+    int len = abs(r_neg) + abs(r_pos) - 1;
+    int ends = (r_neg > 0) + (r_pos > 0);
+    if (ends == 0)
+        return 1.0f;
+    float from_neg = ((float)(r_neg - 1) + f) / (float)len;
+    float from_pos = ((float)(r_pos - 1) + (1.0f - f)) / (float)len;
+    if (ends == 2)
+        return from_neg < from_pos ? from_neg : from_pos;
+    return r_neg > 0 ? from_neg : from_pos;
+}
+
+/* Listing 4, §4.1: silhouette recovery for a lit edge fragment.
+ * dxq, dyq are the compressed discontinuities of Eq. 4 in quarters
+ * (3 = 0.75 = edges on both sides of the axis); cx, cy the Eq. 5 codes. */
+static double silhouette_visibility(int dxq, int dyq, int cx, int cy, float nx, float ny)
+{
+    if (dxq == 3 || dyq == 3)      /* short U or O shape */
+        return 0.0;
+    if (cx == 1 || cy == 1)        /* long U or O shape */
+        return 0.0;
+    if (cx == -1 || cy == -1)      /* I shape */
+        return 1.0;
+    /* L shape: shadow below the revectorisation line ny = 1 - nx, a point on
+     * the line stays lit */
+    float line = 1.0f - nx;
+    return ny < line ? 0.0 : 1.0;
+}
+
+/* Listing 5, §4.2: filtering (fake penumbra) for an edge fragment on either
+ * side of the edge; dz = 1 - s.  R11 for the I-shape test. */
+static double filter_visibility(int dxq, int dyq, int dz, int cx, int cy, double nx, double ny)
+{
+    double sgn = 1.0 - 2.0 * (double)dz;
+    if (dxq == 3 && dyq == 3)      /* short O shape: close it */
+        return (double)dz;
+    if (cx == 1 && cy == 1)        /* long O shape */
+        return (double)dz;
+    if (cx == 1)                   /* U shape open along y */
+        return (double)dz + sgn * ny;
+    if (cy == 1)                   /* U shape open along x */
+        return (double)dz + sgn * nx;
+    if (cx == -1 || cy == -1)      /* I shape: the plain shadow test */
+        return 1.0 - (double)dz;
+    double v = (double)dz + sgn * ny + sgn * nx;   /* L shape */
+    if (v < 0.0) v = 0.0;
+    if (v > 1.0) v = 1.0;
+    return v;
+}
+
+/* Listing 1 with Listings 2-5: visibility of one fragment.
+ * Writes the visibility, the uint16 code, and optionally the four walks and
+ * the normalised vector (nx, ny, cx, cy).
+ * Code bits: 0-3 discontinuity directions (left, right, +y, -y), 4 = d.z
+ * (shadow-test failed), 5-6 ends found along x (0..2), 7-8 ends found along
+ * y, 9 = the fragment went through the edge traversal. */
+static void rbsm_fragment(const sm_t *sm, float x, float y, float pz, int mode, int max_dist,
+                          double *vis_out, uint16_t *code_out, int32_t rd_out[4], double nrd_out[4])
+{
+    /* R1, R17: texel and in-texel offset from the single-precision product */
+    float u = x * (float)sm->width;
+    float v = y * (float)sm->height;
+    float fu = floorf(u), fv = floorf(v);
+    float fx = u - fu, fy = v - fv;
+    int64_t i = (int64_t)fu, j = (int64_t)fv;
+    if (i < 0) i = 0;
+    if (i > sm->width - 1) i = sm->width - 1;
+    if (j < 0) j = 0;
+    if (j > sm->height - 1) j = sm->height - 1;
+
+    int dirs[4];
+    int s0 = discontinuity4(sm, i, j, pz, dirs);
+    int dz = 1 - s0;
+    /* Eq. 4 in quarters: d.x = (2 d_left + d_right)/4, d.y = (2 d_+y + d_-y)/4 */
+    int dxq = 2 * dirs[0] + dirs[1];
+    int dyq = 2 * dirs[2] + dirs[3];
+
+    uint16_t code = (uint16_t)(dirs[0] | (dirs[1] << 1) | (dirs[2] << 2) | (dirs[3] << 3) | (dz << 4));
+    int32_t rd[4] = {0, 0, 0, 0};
+    double nrd[4] = {0.0, 0.0, 0.0, 0.0};
+    double vis;
+
+    if (mode == ORACLE_MODE_SILHOUETTE && s0 == 0) {
+        /* Listing 1: shadowed fragments stay shadowed in silhouette recovery */
+        vis = 0.0;
+    } else if (dxq == 0 && dyq == 0) {
+        /* Listing 1: outside a shadow edge the shadow test is the answer */
+        vis = (double)s0;
+    } else {
+        /* R6: the four walks */
+        rd[0] = traverse_edge(sm, i, j, pz, s0, dirs, -1, 0, max_dist);
+        rd[1] = traverse_edge(sm, i, j, pz, s0, dirs, +1, 0, max_dist);
+        rd[2] = traverse_edge(sm, i, j, pz, s0, dirs, 0, -1, max_dist);
+        rd[3] = traverse_edge(sm, i, j, pz, s0, dirs, 0, +1, max_dist);
+        int cx, cy;
+        double nx = axis_position_f64(rd[0], rd[1], (double)fx, &cx);
+        double ny = axis_position_f64(rd[2], rd[3], (double)fy, &cy);
+        nrd[0] = nx;
+        nrd[1] = ny;
+        nrd[2] = (double)cx;
+        nrd[3] = (double)cy;
+        int ex = (rd[0] > 0) + (rd[1] > 0);
+        int ey = (rd[2] > 0) + (rd[3] > 0);
+        code = (uint16_t)(code | (ex << 5) | (ey << 7) | (1 << 9));
+        if (mode == ORACLE_MODE_SILHOUETTE) {
+            float nx32 = axis_position_f32(rd[0], rd[1], fx);
+            float ny32 = axis_position_f32(rd[2], rd[3], fy);
+            vis = silhouette_visibility(dxq, dyq, cx, cy, nx32, ny32);
+        } else {
+            vis = filter_visibility(dxq, dyq, dz, cx, cy, nx, ny);
+        }
+    }
+    *vis_out = vis;
+    if (code_out)
+        *code_out = code;
+    if (rd_out)
+        for (int k = 0; k < 4; ++k) rd_out[k] = rd[k];
+    if (nrd_out)
+        for (int k = 0; k < 4; ++k) nrd_out[k] = nrd[k];
+}
+
+/* Evaluate n fragments.  Returns 0, or -1 on invalid arguments.
+ * rd (n*4 int32), nrd (n*4 double) and codes may be NULL. */
+int oracle_rbsm_eval(const float *depth, int32_t width, int32_t height, int64_t pitch,
+                     const float *px, const float *py, const float *pz, int64_t n,
+                     int32_t mode, int32_t max_dist,
+                     double *vis, uint16_t *codes, int32_t *rd, double *nrd)
+{
+    if (!depth || width < 1 || height < 1 || pitch < width || n < 0 || max_dist < 1)
+        return -1;
+    if (n > 0 && (!px || !py || !pz || !vis))
+        return -1;
+    if (mode != ORACLE_MODE_SILHOUETTE && mode != ORACLE_MODE_FILTER)
+        return -1;
+    sm_t sm = {depth, width, height, pitch};
+    for (int64_t t = 0; t < n; ++t) {
+        rbsm_fragment(&sm, px[t], py[t], pz[t], mode, max_dist, &vis[t],
+                      codes ? &codes[t] : NULL,
+                      rd ? &rd[4 * t] : NULL,
+                      nrd ? &nrd[4 * t] : NULL);
+    }
+    return 0;
+}
