@@ -44,7 +44,8 @@
  *       -(MAXDIST + 1).
  *   R15 the equality tests on d and nrd compare exact codes.
  *   R17 a fragment outside [0,1) is clamped to the edge texel; its in-texel
- *       offset is still frac(x*W).
+ *       offset is still frac(x*W).  The clamp is taken on the float texel
+ *       coordinate, so a NaN coordinate maps to texel 0.
  */
 #include <math.h>
 #include <stdint.h>
@@ -221,11 +222,10 @@ static void rbsm_fragment(const sm_t *sm, float x, float y, float pz, int mode, 
     float v = y * (float)sm->height;
     float fu = floorf(u), fv = floorf(v);
     float fx = u - fu, fy = v - fv;
-    int64_t i = (int64_t)fu, j = (int64_t)fv;
-    if (i < 0) i = 0;
-    if (i > sm->width - 1) i = sm->width - 1;
-    if (j < 0) j = 0;
-    if (j > sm->height - 1) j = sm->height - 1;
+    /* clamp while still a float (fmaxf/fminf pick the non-NaN operand, so a
+     * NaN coordinate lands on the first texel) */
+    int64_t i = (int64_t)fminf(fmaxf(fu, 0.0f), (float)(sm->width - 1));
+    int64_t j = (int64_t)fminf(fmaxf(fv, 0.0f), (float)(sm->height - 1));
 
     int dirs[4];
     int s0 = discontinuity4(sm, i, j, pz, dirs);
