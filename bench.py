@@ -1,0 +1,441 @@
+#!/usr/bin/env python3
+"""Throughput of the RBSM per-fragment path on one GB300 (or N replicas).
+
+Workload (the 3840x2160 configuration): 32 frames of a moving light, each
+frame an 8192^2 float32 shadow map rasterised from 200 occluders and
+3840x2160 light-space fragments of a static camera.  One step evaluates every
+fragment of every frame against its frame's map, giving each fragment both
+answers of the method: the revectorised hard shadow (silhouette recovery,
+Listing 4) and the RSMSS fake penumbra (filtering, Listing 5), in ONE
+persistent batched launch (rbsm_batch_run, mode BOTH).  Inputs are larger
+than L2 (about 11 GB per step), so no L2 flush is needed between steps.
+
+Printed: one JSON line with the metric (Gfragments/s, whole job), the
+roofline of the batched kernel against the measured HBM copy bandwidth, an
+end-to-end figure through the public API with host buffers, and the CPU
+oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gfragments/s visibility at 3840x2160"
+UNIT = "Gfragments/s"
+BYTES_PER_FRAGMENT = 12 + 4 + 4     # x, y, z in; silhouette and filter visibility out
+BYTES_PER_TEXEL = 4                 # each unique centre texel read once
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ["paper_1711_07793_gb300/csrc/rbsm_device.cuh", "paper_1711_07793_gb300/csrc/rbsm_batch.cu"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "batch_kernel_c5_traffic.md")
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--frames", type=int, default=32, help="frames per step (32 = the full workload)")
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--skip-e2e", action="store_true", help="profiling runs only")
+    p.add_argument("--skip-cpu", action="store_true", help="profiling runs only")
+    p.add_argument("--tile-threads", type=int, default=0)
+    p.add_argument("--ctas-per-sm", type=int, default=0)
+    return p.parse_args(argv)
+
+
+# ------------------------------------------------------------ distributed --
+
+def dist_env():
+    """(rank, world, local_rank) from torchrun's environment (1 process: 0, 1, 0)."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(value, world):
+    """Largest value over all ranks (the whole job ends with its slowest rank)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ peaks --
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(frames):
+    """DRAM bytes per launch from the committed ncu summary, scaled to
+    `frames`, or None when the summary is missing or the kernel changed."""
+    try:
+        text = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    src = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    per = re.search(r"dram_bytes_per_frame:\s*([0-9.eE+]+)", text)
+    if not src or not per or src.group(1) != kernel_source_hash():
+        return None
+    return float(per.group(1)) * frames
+
+
+# ----------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of one GPU while a region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self, t0, t1):
+        sel = [p for t, p in self.samples if t0 - 0.2 <= t <= t1 + 0.2]
+        if not sel:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(p[0]) for p in sel if num(p[0]) is not None]
+        mx = [num(p[1]) for p in sel if num(p[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for p in sel for k in range(4) if p[4 + k].lower() == "active"})
+        power = [num(p[2]) for p in sel if num(p[2]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sel), "power_w_max": max(power) if power else None}
+
+
+def smi_gpu_id(local_rank):
+    """An id nvidia-smi accepts for this process's GPU: its UUID when torch
+    reports one, else the CUDA_VISIBLE_DEVICES entry, else the index."""
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(local_rank).uuid)
+        if re.fullmatch(r"(GPU-)?[0-9a-fA-F-]{36}", u):
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except (AttributeError, RuntimeError):
+        pass
+    cvd = [s.strip() for s in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if s.strip()]
+    if local_rank < len(cvd):
+        return cvd[local_rank]
+    return str(local_rank)
+
+
+# --------------------------------------------------------------- workload --
+
+def unique_texels(x, y, size):
+    """Number of distinct centre texels the fragments land on (float32
+    texel coordinates, clamp-to-edge), for the algorithmic map bytes."""
+    import numpy as np
+    u = np.clip(np.floor(x * np.float32(size)), 0, size - 1).astype(np.int64)
+    v = np.clip(np.floor(y * np.float32(size)), 0, size - 1).astype(np.int64)
+    seen = np.zeros(size * size, dtype=bool)
+    seen[v * size + u] = True
+    return int(seen.sum())
+
+
+def make_workload(frames, seed, pin=True):
+    """Host tensors (pinned) of `frames` frames of the 8192^2 / 3840x2160
+    moving-light workload, plus per-frame unique-texel counts."""
+    import numpy as np
+    import torch
+    import rbsm_scenes as sc
+    c5 = sc.Config5(seed)
+    n = c5.screen[0] * c5.screen[1]
+    out = []
+    for f in range(frames):
+        depth = torch.empty((c5.size, c5.size), dtype=torch.float32, pin_memory=pin)
+        xyz = torch.empty((3, n), dtype=torch.float32, pin_memory=pin)
+        dn, xn = depth.numpy(), xyz.numpy()
+        fr = c5.frame(f, out_depth=dn, out_xyz=(xn[0], xn[1], xn[2]))
+        out.append({"depth": depth, "xyz": xyz, "U": unique_texels(xn[0], xn[1], c5.size),
+                    "sphere_fraction": fr.meta["sphere_fraction"]})
+    return c5, out
+
+
+# ------------------------------------------------------------ CPU oracle --
+
+def oracle_throughput(host_frames, max_seconds=30.0):
+    """The oracle as it stands, chunked over every host core (ctypes releases
+    the GIL), on whole frames until max_seconds: Gfragments/s where a
+    fragment gets both answers (silhouette and filtering)."""
+    import numpy as np
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import rbsm as orc
+    cores = os.cpu_count() or 1
+    done = 0
+    frames_done = 0
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        for fr in host_frames:
+            depth = fr["depth"].numpy()
+            xyz = fr["xyz"].numpy()
+            n = xyz.shape[1]
+            bounds = np.linspace(0, n, cores + 1).astype(np.int64)
+
+            def work(k):
+                a, b = bounds[k], bounds[k + 1]
+                for mode in (orc.MODE_SILHOUETTE, orc.MODE_FILTER):
+                    orc.evaluate(depth, xyz[0, a:b], xyz[1, a:b], xyz[2, a:b], mode)
+                return b - a
+
+            done += sum(ex.map(work, range(cores)))
+            frames_done += 1
+            if time.perf_counter() - t0 > max_seconds:
+                break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d of 32 frames, every fragment, both visibility functions, %.1f s" % (frames_done, dt)}
+
+
+# ------------------------------------------------------------------- ours --
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1711_07793_gb300 import api
+    from paper_1711_07793_gb300 import build as lib_build
+    lib_build.build()
+
+    torch.cuda.set_device(local_rank)
+    device = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+
+    c5, host = make_workload(args.frames, args.seed + 1000 * rank)
+    n_frag = c5.screen[0] * c5.screen[1]
+    frames = len(host)
+    maps = [h["depth"].to(device, non_blocking=True) for h in host]
+    xyz = [h["xyz"].to(device, non_blocking=True) for h in host]
+    jobs = [api.Job(k, xyz[k][0], xyz[k][1], xyz[k][2], mode=3) for k in range(frames)]
+    batch = api.Batch(maps, jobs, tile_threads=args.tile_threads, ctas_per_sm=args.ctas_per_sm)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+
+    # warm-up, then exactly K timed steps, one CUDA event pair per launch
+    for _ in range(args.warmup):
+        api.rbsm_batch_run(batch)
+    sampler = ClockSampler(smi_gpu_id(local_rank))
+    sampler.start()
+    time.sleep(0.5)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for k in range(args.steps):
+        starts[k].record(stream)
+        api.rbsm_batch_run(batch)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    barrier(world)
+    sampler.stop()
+    clocks = sampler.summary(t0, t1)
+    assert api.rbsm_batch_status(batch) == 0
+    launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = starts[0].elapsed_time(ends[-1])
+    total_ms = max_over_ranks(total_ms, world)
+    ms_per_step = total_ms / args.steps
+
+    # roofline of the batched kernel (the only kernel of a step)
+    peak, peak_kind = load_peaks()
+    bytes_per_launch = sum(BYTES_PER_FRAGMENT * n_frag + BYTES_PER_TEXEL * h["U"] for h in host)
+    mean_launch_ms = statistics.mean(launch_ms)
+    achieved = bytes_per_launch / (mean_launch_ms * 1e-3) / 1e9
+    traffic = recorded_traffic(frames)
+
+    # end to end through the public API: pinned host -> device copies of the
+    # step's maps and fragments, the batched launch, device -> host answers
+    e2e = None
+    if not args.skip_e2e:
+        out_sil = [torch.empty(n_frag, dtype=torch.float32, pin_memory=True) for _ in range(frames)]
+        out_fil = [torch.empty(n_frag, dtype=torch.float32, pin_memory=True) for _ in range(frames)]
+        h2d = sum(h["depth"].numel() * 4 + h["xyz"].numel() * 4 for h in host)
+        d2h = frames * n_frag * 8
+
+        def e2e_step():
+            for k in range(frames):
+                maps[k].copy_(host[k]["depth"], non_blocking=True)
+                xyz[k].copy_(host[k]["xyz"], non_blocking=True)
+            api.rbsm_batch_run(batch)
+            for k in range(frames):
+                out_sil[k].copy_(jobs[k].vis_silhouette, non_blocking=True)
+                out_fil[k].copy_(jobs[k].vis_filter, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.e2e_steps, world)
+        e2e = {"value": world * frames * n_frag / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        cpu = oracle_throughput(host[:4])
+
+    line = {
+        "metric": METRIC, "value": world * frames * n_frag / (ms_per_step * 1e-3) / 1e9, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "C5: %d frames x 3840x2160 fragments, 8192^2 fp32 maps, moving light, "
+                               "silhouette + RSMSS per fragment" % frames,
+                   "frames": frames, "screen": list(c5.screen), "map": c5.size, "mode": "both",
+                   "batched": "one persistent launch per step (rbsm_batch_run)", "max_dist": 16,
+                   "l2": "inputs larger than L2 (%.1f GB per step), no flush" % (
+                       sum(h["depth"].numel() * 4 + h["xyz"].numel() * 4 for h in host) / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "tile_threads": args.tile_threads or 256, "ctas_per_sm": args.ctas_per_sm or "occupancy"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
+                     else "fallback 6800 GB/s",
+                     "traffic": traffic, "kernel": "rbsm::batch_kernel<256>",
+                     "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "mean_launch_ms": mean_launch_ms, "min_launch_ms": min(launch_ms)},
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "edge": {"unique_texels_per_frame": statistics.mean(h["U"] for h in host)},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# -------------------------------------------------------------- reference --
+
+def run_reference(args, rank, world):
+    """The oracle as it stands on the host cores: each step is one frame of
+    the workload (every fragment, both visibility functions)."""
+    if rank != 0:
+        return
+    import numpy as np
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import rbsm as orc
+    import rbsm_scenes as sc
+    c5 = sc.Config5(args.seed)
+    fr = c5.frame(0)
+    cores = os.cpu_count() or 1
+    bounds = np.linspace(0, fr.n, cores + 1).astype(np.int64)
+
+    def work(k):
+        a, b = bounds[k], bounds[k + 1]
+        for mode in (orc.MODE_SILHOUETTE, orc.MODE_FILTER):
+            orc.evaluate(fr.depth, fr.x[a:b], fr.y[a:b], fr.z[a:b], mode)
+
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        for _ in range(args.warmup):
+            list(ex.map(work, range(cores)))
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            list(ex.map(work, range(cores)))
+        dt = time.perf_counter() - t0
+    ms = dt * 1e3 / args.steps
+    value = fr.n / (ms * 1e-3) / 1e9
+    sample = "frame 0 of 32 (3840x2160 fragments, 8192^2 map) per step, both visibility functions"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "C5: 32 frames x 3840x2160 fragments, 8192^2 fp32 maps, moving light, "
+                                   "silhouette + RSMSS per fragment", "sampled": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, world, local_rank = dist_env()
+    if world != args.gpus and world == 1 and args.gpus > 1:
+        raise SystemExit("--gpus %d needs torchrun with %d processes" % (args.gpus, args.gpus))
+    if args.warmup < 0 or args.steps < 1:
+        raise SystemExit("--steps must be >= 1 and --warmup >= 0")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

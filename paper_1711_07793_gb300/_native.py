@@ -1,0 +1,117 @@
+"""ctypes view of the C ABI in include/rbsm.h (no compute here).
+
+The library is loaded from this package's _build/ directory and nowhere
+else.  There is no fallback: when librbsm.so is missing or cannot be loaded,
+``lib()`` raises, so nothing can silently run a different implementation.
+"""
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "librbsm.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "rbsm.h")
+
+RBSM_OK = 0
+RBSM_ERR_ARG = -1
+RBSM_ERR_CUDA = -2
+RBSM_ERR_TIMEOUT = -3
+RBSM_ERR_WORKSPACE = -4
+
+RBSM_MODE_SILHOUETTE = 1
+RBSM_MODE_FILTER = 2
+RBSM_MODE_BOTH = 3
+RBSM_MAXDIST_DEFAULT = 16
+RBSM_BATCH_MAX_MAPS = 64
+RBSM_BATCH_MAX_JOBS = 256
+
+
+class rbsm_map(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_void_p), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("pitch", ctypes.c_int64)]
+
+
+class rbsm_frags(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("z", ctypes.c_void_p), ("n", ctypes.c_int64)]
+
+
+class rbsm_params(ctypes.Structure):
+    _fields_ = [("max_dist", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class rbsm_job(ctypes.Structure):
+    _fields_ = [("map", ctypes.c_int32), ("mode", ctypes.c_int32), ("frags", rbsm_frags),
+                ("vis_silhouette", ctypes.c_void_p), ("vis_filter", ctypes.c_void_p),
+                ("codes", ctypes.c_void_p)]
+
+
+class rbsm_batch(ctypes.Structure):
+    _fields_ = [("maps", ctypes.POINTER(rbsm_map)), ("n_maps", ctypes.c_int32),
+                ("jobs", ctypes.POINTER(rbsm_job)), ("n_jobs", ctypes.c_int32),
+                ("params", rbsm_params), ("tile_threads", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32)]
+
+
+class RBSMError(RuntimeError):
+    def __init__(self, fn, code, cuda_error=0):
+        msg = "%s failed: %s (%d)" % (fn, status_string(code), code)
+        if code == RBSM_ERR_CUDA:
+            msg += ", cudaError %d" % cuda_error
+        super().__init__(msg)
+        self.code = code
+        self.cuda_error = cuda_error
+
+
+_lib = None
+_P = ctypes.POINTER
+
+
+def _declare(lib):
+    vp, i32 = ctypes.c_void_p, ctypes.c_int
+    for name in ("rbsm_visibility", "rsmss_filter"):
+        f = getattr(lib, name)
+        f.restype = i32
+        f.argtypes = [_P(rbsm_map), _P(rbsm_frags), vp, vp, _P(rbsm_params), vp]
+    lib.rbsm_batch_workspace_size.restype = i32
+    lib.rbsm_batch_workspace_size.argtypes = [_P(rbsm_batch), _P(ctypes.c_size_t)]
+    lib.rbsm_batch_run.restype = i32
+    lib.rbsm_batch_run.argtypes = [_P(rbsm_batch), vp, ctypes.c_size_t, vp]
+    lib.rbsm_batch_status.restype = i32
+    lib.rbsm_batch_status.argtypes = [vp, _P(ctypes.c_int)]
+    lib.rbsm_status_string.restype = ctypes.c_char_p
+    lib.rbsm_status_string.argtypes = [i32]
+    lib.rbsm_last_cuda_error.restype = i32
+    lib.rbsm_version.restype = i32
+
+
+def lib():
+    """The loaded librbsm.so (raises when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("librbsm.so is not built (%s); run paper_1711_07793_gb300.build.build()"
+                               % LIB_PATH)
+        l = ctypes.CDLL(LIB_PATH)
+        _declare(l)
+        _lib = l
+    return _lib
+
+
+def status_string(code):
+    try:
+        return lib().rbsm_status_string(code).decode()
+    except RuntimeError:
+        return "status %d" % code
+
+
+def check(fn, code):
+    if code != RBSM_OK:
+        raise RBSMError(fn, code, lib().rbsm_last_cuda_error() if code == RBSM_ERR_CUDA else 0)
+
+
+def header_functions(path=HEADER):
+    """Names of the functions include/rbsm.h declares."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return re.findall(r"^[A-Za-z_][\w \*]*?\b(rbsm\w*|rsmss\w*)\s*\(", text, flags=re.M)

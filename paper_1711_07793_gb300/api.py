@@ -1,0 +1,165 @@
+"""Python binding of librbsm with the C ABI's names (argument marshalling only).
+
+Tensors are torch tensors: float32 shadow maps of shape (height, width) with
+unit stride along width, and float32 fragment planes x, y, z of shape (n,).
+CUDA tensors are passed to the library as device pointers on the current
+torch stream.  CPU tensors are accepted too: they are copied to the GPU,
+evaluated there and the answers copied back (the host-buffer path); every
+step of the method runs in the library's kernels either way.
+"""
+import ctypes
+
+import torch
+
+from . import _native as N
+
+
+def _stream_handle(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_plane(name, t, n=None):
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or t.dim() != 1:
+        raise TypeError("%s must be a 1-D float32 tensor" % name)
+    if not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.stride(0) != 1:
+        raise ValueError("%s must be contiguous" % name)
+    if n is not None and t.shape[0] != n:
+        raise ValueError("%s has %d elements, expected %d" % (name, t.shape[0], n))
+
+
+def map_desc(depth):
+    """rbsm_map for a (height, width) float32 CUDA tensor with unit inner stride."""
+    if not isinstance(depth, torch.Tensor) or depth.dtype != torch.float32 or depth.dim() != 2:
+        raise TypeError("depth must be a 2-D float32 tensor")
+    if not depth.is_cuda:
+        raise TypeError("depth must be a CUDA tensor")
+    if depth.stride(1) != 1 or depth.stride(0) < depth.shape[1]:
+        raise ValueError("depth rows must be contiguous (pitch >= width)")
+    return N.rbsm_map(depth.data_ptr(), depth.shape[1], depth.shape[0], depth.stride(0))
+
+
+def frags_desc(x, y, z):
+    _check_plane("x", x)
+    n = x.shape[0]
+    _check_plane("y", y, n)
+    _check_plane("z", z, n)
+    return N.rbsm_frags(x.data_ptr(), y.data_ptr(), z.data_ptr(), n)
+
+
+def _params(max_dist):
+    return N.rbsm_params(int(max_dist), 0)
+
+
+def _host_roundtrip(fn, depth, x, y, z, codes, max_dist):
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d = depth.to(dev, non_blocking=True)
+    xd, yd, zd = (t.to(dev, non_blocking=True) for t in (x, y, z))
+    vis, cod = fn(d, xd, yd, zd, codes=codes, max_dist=max_dist)
+    vis_h = torch.empty(vis.shape, dtype=vis.dtype, pin_memory=True)
+    vis_h.copy_(vis, non_blocking=True)
+    cod_h = None
+    if cod is not None:
+        cod_h = torch.empty(cod.shape, dtype=cod.dtype, pin_memory=True)
+        cod_h.copy_(cod, non_blocking=True)
+    torch.cuda.current_stream().synchronize()
+    return vis_h, cod_h
+
+
+def _single(cfn, fname, depth, x, y, z, vis=None, codes=False, max_dist=N.RBSM_MAXDIST_DEFAULT, stream=None):
+    if not depth.is_cuda:
+        return _host_roundtrip(lambda *a, **k: _single(cfn, fname, *a, **k), depth, x, y, z, codes, max_dist)
+    m = map_desc(depth)
+    f = frags_desc(x, y, z)
+    n = f.n
+    if vis is None:
+        vis = torch.empty(n, dtype=torch.float32, device=x.device)
+    else:
+        _check_plane("vis", vis, n)
+    cod = None
+    if codes is True:
+        cod = torch.empty(n, dtype=torch.int16, device=x.device)
+    elif isinstance(codes, torch.Tensor):
+        cod = codes
+        if cod.dtype not in (torch.int16, torch.uint16) or cod.numel() != n or not cod.is_cuda:
+            raise TypeError("codes must be an int16/uint16 CUDA tensor of n elements")
+    p = _params(max_dist)
+    rc = cfn(ctypes.byref(m), ctypes.byref(f), ctypes.c_void_p(vis.data_ptr()),
+             ctypes.c_void_p(cod.data_ptr() if cod is not None else 0), ctypes.byref(p), _stream_handle(stream))
+    N.check(fname, rc)
+    return vis, cod
+
+
+def rbsm_visibility(depth, x, y, z, vis=None, codes=False, max_dist=N.RBSM_MAXDIST_DEFAULT, stream=None):
+    """Silhouette recovery (Listing 4): returns (vis, codes or None).
+    codes=True allocates an int16 code plane (bit layout in include/rbsm.h)."""
+    return _single(N.lib().rbsm_visibility, "rbsm_visibility", depth, x, y, z, vis, codes, max_dist, stream)
+
+
+def rsmss_filter(depth, x, y, z, vis=None, codes=False, max_dist=N.RBSM_MAXDIST_DEFAULT, stream=None):
+    """Revectorization-based shadow filtering (Listing 5): returns (vis, codes or None)."""
+    return _single(N.lib().rsmss_filter, "rsmss_filter", depth, x, y, z, vis, codes, max_dist, stream)
+
+
+class Job:
+    """One fragment set against one map of a batch.  Outputs are allocated
+    when not given: vis_silhouette / vis_filter per the mode."""
+
+    def __init__(self, map_index, x, y, z, mode=N.RBSM_MODE_BOTH, vis_silhouette=None, vis_filter=None,
+                 codes=None):
+        self.map_index, self.mode = int(map_index), int(mode)
+        self.x, self.y, self.z = x, y, z
+        n = x.shape[0]
+        if (mode & 1) and vis_silhouette is None:
+            vis_silhouette = torch.empty(n, dtype=torch.float32, device=x.device)
+        if (mode & 2) and vis_filter is None:
+            vis_filter = torch.empty(n, dtype=torch.float32, device=x.device)
+        if codes is True:
+            codes = torch.empty(n, dtype=torch.int16, device=x.device)
+        self.vis_silhouette, self.vis_filter, self.codes = vis_silhouette, vis_filter, codes
+
+    def desc(self):
+        f = frags_desc(self.x, self.y, self.z)
+        ptr = lambda t: t.data_ptr() if t is not None else 0
+        return N.rbsm_job(self.map_index, self.mode, f, ptr(self.vis_silhouette), ptr(self.vis_filter),
+                          ptr(self.codes))
+
+
+class Batch:
+    """Descriptor arrays of a batched launch, kept alive with their tensors."""
+
+    def __init__(self, maps, jobs, max_dist=N.RBSM_MAXDIST_DEFAULT, tile_threads=0, ctas_per_sm=0):
+        self.maps, self.jobs = list(maps), list(jobs)
+        self._maps = (N.rbsm_map * len(self.maps))(*[map_desc(m) for m in self.maps])
+        self._jobs = (N.rbsm_job * len(self.jobs))(*[j.desc() for j in self.jobs])
+        self.desc = N.rbsm_batch(self._maps, len(self.maps), self._jobs, len(self.jobs),
+                                 _params(max_dist), int(tile_threads), int(ctas_per_sm))
+        size = ctypes.c_size_t(0)
+        N.check("rbsm_batch_workspace_size", N.lib().rbsm_batch_workspace_size(ctypes.byref(self.desc),
+                                                                              ctypes.byref(size)))
+        self.workspace_bytes = size.value
+        dev = self.jobs[0].x.device
+        # 256-byte aligned: the caching allocator aligns blocks to 512 bytes
+        self.workspace = torch.zeros(max(self.workspace_bytes, 256) // 4, dtype=torch.int32, device=dev)
+
+    def set_launch(self, tile_threads, ctas_per_sm):
+        self.desc.tile_threads = int(tile_threads)
+        self.desc.ctas_per_sm = int(ctas_per_sm)
+
+
+def rbsm_batch_run(batch, stream=None):
+    """Enqueue one persistent launch over every job of `batch` (a Batch)."""
+    rc = N.lib().rbsm_batch_run(ctypes.byref(batch.desc), ctypes.c_void_p(batch.workspace.data_ptr()),
+                                batch.workspace_bytes, _stream_handle(stream))
+    N.check("rbsm_batch_run", rc)
+    return batch
+
+
+def rbsm_batch_status(batch):
+    """Status word the last completed launch of `batch` recorded."""
+    st = ctypes.c_int(0)
+    N.check("rbsm_batch_status", N.lib().rbsm_batch_status(ctypes.c_void_p(batch.workspace.data_ptr()),
+                                                           ctypes.byref(st)))
+    return st.value

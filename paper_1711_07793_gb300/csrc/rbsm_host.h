@@ -1,0 +1,52 @@
+// Host helpers shared by the translation units of the RBSM library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "rbsm.h"
+#include "rbsm_device.cuh"
+
+namespace rbsm {
+
+int cuda_fail(cudaError_t e);
+int check_map(const rbsm_map *m);
+int check_frags(const rbsm_frags *f);
+int check_params(const rbsm_params *p, int *max_dist);
+bool aligned16(const void *p);
+int device_sm_count();
+MapDev to_dev(const rbsm_map &m);
+
+// Per-device cache of "dynamic shared memory attribute set + occupancy" for
+// one kernel.  The attribute is a per-device property, so it is set once on
+// every device the kernel is launched on.
+struct KernelSetup {
+    static constexpr int kMaxDevices = 64;
+    int occupancy[kMaxDevices] = {};
+
+    template <typename Kernel>
+    int get(Kernel kern, int threads, size_t smem, int *occ)
+    {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess)
+            return cuda_fail(e);
+        if (dev < 0 || dev >= kMaxDevices)
+            return cuda_fail(cudaErrorInvalidDevice);
+        if (occupancy[dev] == 0) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess)
+                return cuda_fail(e);
+            int o = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, threads, smem);
+            if (e != cudaSuccess)
+                return cuda_fail(e);
+            if (o < 1)
+                return cuda_fail(cudaErrorInvalidConfiguration);
+            occupancy[dev] = o;
+        }
+        *occ = occupancy[dev];
+        return RBSM_OK;
+    }
+};
+
+}  // namespace rbsm

@@ -1,0 +1,178 @@
+// Single-map entry points rbsm_visibility and rsmss_filter, plus the shared
+// host helpers of the C ABI (argument checks, status strings, device facts).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "rbsm.h"
+#include "rbsm_device.cuh"
+#include "rbsm_host.h"
+
+namespace rbsm {
+
+thread_local int g_last_cuda_error = 0;
+
+int cuda_fail(cudaError_t e)
+{
+    g_last_cuda_error = (int)e;
+    return RBSM_ERR_CUDA;
+}
+
+int check_map(const rbsm_map *m)
+{
+    if (!m || !m->depth)
+        return RBSM_ERR_ARG;
+    if (m->width < 1 || m->height < 1 || m->width > RBSM_MAX_EXTENT || m->height > RBSM_MAX_EXTENT)
+        return RBSM_ERR_ARG;
+    if (m->pitch < m->width)
+        return RBSM_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(m->depth) & 3u) != 0)
+        return RBSM_ERR_ARG;
+    return RBSM_OK;
+}
+
+int check_frags(const rbsm_frags *f)
+{
+    if (!f || f->n < 0)
+        return RBSM_ERR_ARG;
+    if (f->n > 0 && (!f->x || !f->y || !f->z))
+        return RBSM_ERR_ARG;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(f->x) | reinterpret_cast<uintptr_t>(f->y) |
+                        reinterpret_cast<uintptr_t>(f->z);
+    if (f->n > 0 && (a & 3u) != 0)
+        return RBSM_ERR_ARG;
+    return RBSM_OK;
+}
+
+int check_params(const rbsm_params *p, int *max_dist)
+{
+    if (!p) {
+        *max_dist = RBSM_MAXDIST_DEFAULT;
+        return RBSM_OK;
+    }
+    if (p->max_dist < 1 || p->max_dist > RBSM_MAXDIST_LIMIT || p->flags != 0)
+        return RBSM_ERR_ARG;
+    *max_dist = p->max_dist;
+    return RBSM_OK;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int device_sm_count()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return 0;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return sms;
+}
+
+MapDev to_dev(const rbsm_map &m) { return MapDev{m.depth, m.width, m.height, (long long)m.pitch}; }
+
+// ---------------------------------------------------------------- kernel --
+
+template <int MODE, bool CODES, int kThreads>
+__global__ void __launch_bounds__(kThreads)
+plain_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict__ y,
+             const float *__restrict__ z, long long n, float *__restrict__ sil,
+             float *__restrict__ fil, uint16_t *__restrict__ codes, int max_dist, bool vec)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto &sm = *reinterpret_cast<TileSmem<kThreads> *>(smem_raw);
+    constexpr long long kTile = TileSmem<kThreads>::kTile;
+    TileIO io{x, y, z, sil, fil, codes, n, 0, vec};
+    for (long long first = (long long)blockIdx.x * kTile; first < n; first += (long long)gridDim.x * kTile) {
+        io.first = first;
+        process_tile<MODE, CODES, kThreads>(m, io, max_dist, sm);
+    }
+}
+
+template <int MODE, bool CODES>
+int launch_plain(const rbsm_map &map, const rbsm_frags &f, float *sil, float *fil, uint16_t *codes,
+                 int max_dist, cudaStream_t stream)
+{
+    constexpr int kThreads = 256;
+    constexpr long long kTile = TileSmem<kThreads>::kTile;
+    const size_t smem = sizeof(TileSmem<kThreads>);
+    auto kern = plain_kernel<MODE, CODES, kThreads>;
+    static KernelSetup setup;
+    int occupancy = 0;
+    int rc = setup.get(kern, kThreads, smem, &occupancy);
+    if (rc != RBSM_OK)
+        return rc;
+    const int sms = device_sm_count();
+    if (sms <= 0)
+        return cuda_fail(cudaErrorNoDevice);
+    const long long tiles = (f.n + kTile - 1) / kTile;
+    long long grid = (long long)sms * occupancy;
+    if (grid > tiles)
+        grid = tiles;
+    bool vec = aligned16(f.x) && aligned16(f.y) && aligned16(f.z);
+    if (MODE & 1) vec = vec && aligned16(sil);
+    if (MODE & 2) vec = vec && aligned16(fil);
+    if (CODES) vec = vec && aligned16(codes);
+    kern<<<(unsigned)grid, kThreads, smem, stream>>>(to_dev(map), f.x, f.y, f.z, f.n, sil, fil, codes,
+                                                     max_dist, vec);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    return RBSM_OK;
+}
+
+int plain_entry(int mode, const rbsm_map *map, const rbsm_frags *frags, float *vis, uint16_t *codes,
+                const rbsm_params *params, void *stream)
+{
+    int rc, max_dist;
+    if ((rc = check_map(map)) != RBSM_OK) return rc;
+    if ((rc = check_frags(frags)) != RBSM_OK) return rc;
+    if ((rc = check_params(params, &max_dist)) != RBSM_OK) return rc;
+    if (frags->n > 0 && !vis)
+        return RBSM_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(vis) & 3u) != 0 || (reinterpret_cast<uintptr_t>(codes) & 1u) != 0)
+        return RBSM_ERR_ARG;
+    if (frags->n == 0)
+        return RBSM_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (mode == RBSM_MODE_SILHOUETTE)
+        return codes ? launch_plain<1, true>(*map, *frags, vis, nullptr, codes, max_dist, s)
+                     : launch_plain<1, false>(*map, *frags, vis, nullptr, nullptr, max_dist, s);
+    return codes ? launch_plain<2, true>(*map, *frags, nullptr, vis, codes, max_dist, s)
+                 : launch_plain<2, false>(*map, *frags, nullptr, vis, nullptr, max_dist, s);
+}
+
+}  // namespace rbsm
+
+extern "C" {
+
+int rbsm_visibility(const rbsm_map *map, const rbsm_frags *frags, float *vis, uint16_t *codes,
+                    const rbsm_params *params, void *stream)
+{
+    return rbsm::plain_entry(RBSM_MODE_SILHOUETTE, map, frags, vis, codes, params, stream);
+}
+
+int rsmss_filter(const rbsm_map *map, const rbsm_frags *frags, float *vis, uint16_t *codes,
+                 const rbsm_params *params, void *stream)
+{
+    return rbsm::plain_entry(RBSM_MODE_FILTER, map, frags, vis, codes, params, stream);
+}
+
+const char *rbsm_status_string(int code)
+{
+    switch (code) {
+    case RBSM_OK: return "ok";
+    case RBSM_ERR_ARG: return "invalid argument";
+    case RBSM_ERR_CUDA: return "CUDA error";
+    case RBSM_ERR_TIMEOUT: return "device-side wait timed out";
+    case RBSM_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+    default: return "unknown status";
+    }
+}
+
+int rbsm_last_cuda_error(void) { return rbsm::g_last_cuda_error; }
+
+int rbsm_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+"""CPU checks of the C ABI library and of the scene generator (no GPU needed).
+
+The library is cross-compiled for sm_103a here; loading it and rejecting bad
+arguments needs no device.  No test here launches a kernel.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_1711_07793_gb300 import build as B
+    B.build()
+    from paper_1711_07793_gb300 import _native as N
+    N.lib()
+    return N
+
+
+def test_library_exports_every_header_function(native):
+    names = native.header_functions()
+    assert {"rbsm_visibility", "rsmss_filter", "rbsm_batch_run", "rbsm_batch_workspace_size",
+            "rbsm_batch_status", "rbsm_status_string", "rbsm_last_cuda_error", "rbsm_version"} <= set(names)
+    lib = native.lib()
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", native.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    assert set(names) <= exported
+
+
+def test_struct_layouts_match_the_header(native, tmp_path):
+    """ctypes mirrors of the ABI structs have the C compiler's sizes and offsets."""
+    src = tmp_path / "layout.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "rbsm.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(rbsm_map), sizeof(rbsm_frags), sizeof(rbsm_params),
+         sizeof(rbsm_job), sizeof(rbsm_batch));
+  printf("%zu %zu %zu %zu %zu %zu\n", offsetof(rbsm_job, frags), offsetof(rbsm_job, vis_silhouette),
+         offsetof(rbsm_job, codes), offsetof(rbsm_batch, jobs), offsetof(rbsm_batch, params),
+         offsetof(rbsm_batch, ctas_per_sm));
+  return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    sizes = [int(v) for v in lines[0].split()]
+    offs = [int(v) for v in lines[1].split()]
+    N = native
+    assert sizes == [ctypes.sizeof(N.rbsm_map), ctypes.sizeof(N.rbsm_frags), ctypes.sizeof(N.rbsm_params),
+                     ctypes.sizeof(N.rbsm_job), ctypes.sizeof(N.rbsm_batch)]
+    assert offs == [N.rbsm_job.frags.offset, N.rbsm_job.vis_silhouette.offset, N.rbsm_job.codes.offset,
+                    N.rbsm_batch.jobs.offset, N.rbsm_batch.params.offset, N.rbsm_batch.ctas_per_sm.offset]
+
+
+def test_bad_arguments_are_rejected_before_any_cuda_call(native):
+    N = native
+    lib = N.lib()
+    buf = (ctypes.c_float * 64)()
+    addr = ctypes.addressof(buf)
+    good_map = N.rbsm_map(addr, 4, 4, 4)
+    good_frags = N.rbsm_frags(addr, addr, addr, 4)
+    p = N.rbsm_params(16, 0)
+    B = ctypes.byref
+    for fn in (lib.rbsm_visibility, lib.rsmss_filter):
+        assert fn(None, B(good_frags), addr, None, B(p), None) == N.RBSM_ERR_ARG
+        assert fn(B(good_map), None, addr, None, B(p), None) == N.RBSM_ERR_ARG
+        assert fn(B(N.rbsm_map(addr, 0, 4, 4)), B(good_frags), addr, None, B(p), None) == N.RBSM_ERR_ARG
+        assert fn(B(N.rbsm_map(addr, 4, 4, 3)), B(good_frags), addr, None, B(p), None) == N.RBSM_ERR_ARG
+        assert fn(B(N.rbsm_map(addr, 70000, 4, 70000)), B(good_frags), addr, None, B(p), None) == N.RBSM_ERR_ARG
+        assert fn(B(good_map), B(N.rbsm_frags(addr, None, addr, 4)), addr, None, B(p), None) == N.RBSM_ERR_ARG
+        assert fn(B(good_map), B(N.rbsm_frags(addr, addr, addr, -1)), addr, None, B(p), None) == N.RBSM_ERR_ARG
+        assert fn(B(good_map), B(N.rbsm_frags(addr + 1, addr, addr, 4)), addr, None, B(p), None) == N.RBSM_ERR_ARG
+        assert fn(B(good_map), B(good_frags), None, None, B(p), None) == N.RBSM_ERR_ARG
+        assert fn(B(good_map), B(good_frags), addr, None, B(N.rbsm_params(0, 0)), None) == N.RBSM_ERR_ARG
+        assert fn(B(good_map), B(good_frags), addr, None, B(N.rbsm_params(256, 0)), None) == N.RBSM_ERR_ARG
+        assert fn(B(good_map), B(good_frags), addr, None, B(N.rbsm_params(16, 1)), None) == N.RBSM_ERR_ARG
+        # n == 0 enqueues nothing and succeeds without touching the device
+        assert fn(B(good_map), B(N.rbsm_frags(None, None, None, 0)), None, None, None, None) == N.RBSM_OK
+    maps = (N.rbsm_map * 1)(good_map)
+    jobs = (N.rbsm_job * 1)(N.rbsm_job(0, 3, good_frags, addr, addr, None))
+    batch = N.rbsm_batch(maps, 1, jobs, 1, p, 0, 0)
+    size = ctypes.c_size_t(0)
+    assert lib.rbsm_batch_workspace_size(B(batch), B(size)) == N.RBSM_OK and size.value >= 16
+    assert lib.rbsm_batch_run(B(batch), None, 0, None) == N.RBSM_ERR_WORKSPACE
+    assert lib.rbsm_batch_run(B(batch), addr + 4, 4096, None) == N.RBSM_ERR_WORKSPACE
+    for bad in (N.rbsm_job(1, 3, good_frags, addr, addr, None), N.rbsm_job(0, 4, good_frags, addr, addr, None),
+                N.rbsm_job(0, 1, good_frags, None, addr, None), N.rbsm_job(0, 2, good_frags, addr, None, None)):
+        jb = (N.rbsm_job * 1)(bad)
+        assert lib.rbsm_batch_run(B(N.rbsm_batch(maps, 1, jb, 1, p, 0, 0)), addr, 4096, None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_batch_run(B(N.rbsm_batch(maps, 1, jobs, 0, p, 0, 0)), addr, 4096, None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_batch_run(B(N.rbsm_batch(maps, 1, jobs, 1, p, 192, 0)), addr, 4096, None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_batch_run(B(N.rbsm_batch(maps, 65, jobs, 1, p, 0, 0)), addr, 4096, None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_status_string(N.RBSM_ERR_ARG) == b"invalid argument"
+    assert lib.rbsm_version() >= 100
+
+
+def test_generator_is_deterministic_and_in_range():
+    import rbsm_scenes as sc
+    a, b = sc.config1(3), sc.config1(3)
+    assert np.array_equal(a.depth, b.depth) and np.array_equal(a.x, b.x) and np.array_equal(a.z, b.z)
+    c = sc.config1(4)
+    assert not np.array_equal(a.depth, c.depth)
+    assert a.depth.shape == (256, 256) and a.n == 320 * 240
+    assert np.all((a.x > 0) & (a.x < 1) & (a.y > 0) & (a.y < 1))
+    assert np.all(a.z == np.float32(1.0))             # C1 fragments lie on the plane
+    assert 0.01 < np.mean(a.depth < 1) < 0.6
+    f = sc.config2(0, screen=(480, 270))
+    assert f.depth.shape == (2048, 2048) and f.n == 480 * 270
+    assert 0.0 < f.meta["sphere_fraction"] < 1.0
+    # sphere receivers sit 1e-3 in front of their own surface
+    assert np.all(f.z <= 1.0)
+
+
+def test_generator_rasterises_exact_coverage():
+    """A square occluder covers exactly the texels whose centres it contains."""
+    import rbsm_scenes as sc
+    occ = sc.Occluders(np.array([[10.0, 12.0, 1.0, 0.0, 3.2, 2.2]]), np.array([0.5], np.float32))
+    d = sc.raster(occ, 32, 32, 32)
+    ii, jj = np.meshgrid(np.arange(32) + 0.5, np.arange(32) + 0.5)
+    inside = (np.abs(ii - 10) <= 3.2) & (np.abs(jj - 12) <= 2.2)
+    assert np.array_equal(d < 1.0, inside)
+    s = sc.Occluders(spheres=np.array([[16.0, 16.0, 5.0, 0.6]]))
+    d = sc.raster(s, 32, 32, 32)
+    assert d[15, 15] < 0.6 and d[0, 0] == 1.0

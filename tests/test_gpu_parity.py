@@ -1,0 +1,196 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+The bar: discontinuity codes bit-exact; silhouette visibility (0/1, decided
+in float32 on both sides) bit-exact; filtering visibility within 1e-5
+absolute (the oracle computes it in float64, the kernel in float32: one
+rounded add and divide per axis and two adds, all far below 1e-5).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import rbsm as orc  # noqa: E402
+from tests import shapes  # noqa: E402
+
+FILTER_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1711_07793_gb300 import api as A
+    return A
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_gpu(api, depth, x, y, z, mode, max_dist=16, codes=True):
+    d = depth if isinstance(depth, torch.Tensor) else dev(depth)
+    fn = api.rbsm_visibility if mode == orc.MODE_SILHOUETTE else api.rsmss_filter
+    xs, ys, zs = (t if isinstance(t, torch.Tensor) else dev(t) for t in (x, y, z))
+    vis, cod = fn(d, xs, ys, zs, codes=codes, max_dist=max_dist)
+    torch.cuda.synchronize()
+    return vis.cpu().numpy(), (cod.cpu().numpy().view(np.uint16) if cod is not None else None)
+
+
+def assert_parity(vis, codes, ref, mode, where=""):
+    if codes is not None:
+        bad = np.nonzero(codes != ref["codes"])[0]
+        assert bad.size == 0, "%s: %d code mismatches, first %s gpu=%x cpu=%x" % (
+            where, bad.size, bad[0], codes[bad[0]], ref["codes"][bad[0]])
+    v = vis.astype(np.float64)
+    if mode == orc.MODE_SILHOUETTE:
+        bad = np.nonzero(~((v == ref["vis"]) | (np.isnan(v) & np.isnan(ref["vis"]))))[0]
+        assert bad.size == 0, "%s: %d silhouette mismatches" % (where, bad.size)
+    else:
+        diff = np.abs(v - ref["vis"])
+        both_nan = np.isnan(v) & np.isnan(ref["vis"])
+        diff[both_nan] = 0.0
+        assert not np.any(np.isnan(diff)), where
+        assert diff.max(initial=0.0) <= FILTER_TOL, "%s: max |diff| %g" % (where, diff.max())
+
+
+def check_both(api, depth, x, y, z, where, max_dist=16):
+    for mode in (orc.MODE_SILHOUETTE, orc.MODE_FILTER):
+        ref = orc.evaluate(depth, x, y, z, mode, max_dist=max_dist)
+        vis, cod = run_gpu(api, depth, x, y, z, mode, max_dist=max_dist)
+        assert_parity(vis, cod, ref, mode, "%s mode %d" % (where, mode))
+
+
+# ------------------------------------------------------------- workloads --
+
+def test_config1_full(api):
+    import rbsm_scenes as sc
+    for seed in range(3):
+        f = sc.config1(seed)
+        check_both(api, f.depth, f.x, f.y, f.z, "C1 seed %d" % seed)
+
+
+def test_config2_full(api):
+    import rbsm_scenes as sc
+    f = sc.config2(0)
+    check_both(api, f.depth, f.x, f.y, f.z, "C2")
+
+
+def test_config4_full(api):
+    import rbsm_scenes as sc
+    f = sc.config4(0)
+    check_both(api, f.depth, f.x, f.y, f.z, "C4")
+
+
+def test_paper_shapes_on_gpu(api, golden_dir):
+    """The Fig. 3 and staircase inputs of the oracle pins, on the GPU."""
+    from tests.test_oracle_pins import _load_fig3, _inside
+    rects = _load_fig3(golden_dir)
+    for shape in "abcd":
+        ti, tj = np.meshgrid(np.arange(3), np.arange(3), indexing="xy")
+        depth = shapes.embed(_inside(rects[shape]["in"], ti + 0.5, tj + 0.5), 32, 12)
+        X, Y = shapes.fragment_grid(12, 15, 12, 15, [((a + .5) / 5, (b + .5) / 5) for a in range(5) for b in range(5)])
+        x, y = shapes.to_texcoords(X, Y, 32, 32)
+        check_both(api, depth, x, y, np.ones_like(x), "fig3 %s" % shape)
+    for run_len in (1, 3, 7, 16):
+        for orient in shapes.D4_NAMES:
+            mask = shapes.staircase_mask(128, run_len, 8, 40)
+            depth = shapes.d4_map(np.where(mask, shapes.BLOCKER, shapes.LIT).astype(np.float32), orient)
+            X, Y = shapes.fragment_grid(20, 108, 20, 108, [((a + .5) / 4, (b + .5) / 4) for a in range(4) for b in range(4)])
+            Xt, Yt = shapes.d4_points(X, Y, 128, orient)
+            x, y = shapes.to_texcoords(Xt, Yt, 128, 128)
+            check_both(api, depth, x, y, np.ones_like(x), "stair %d %s" % (run_len, orient))
+
+
+# ------------------------------------------------------------- edge cases --
+
+def _random_case(rng, w, h, n, levels=(0.25, 0.5, 0.75, 1.0), spread=0.0):
+    lv = np.array(levels, np.float32)
+    depth = lv[rng.integers(0, len(lv), size=(h, w))]
+    blob = rng.integers(0, 2, size=((h + 3) // 4, (w + 3) // 4)).repeat(4, 0).repeat(4, 1)[:h, :w].astype(bool)
+    depth = np.where(blob, depth, np.float32(1.0)).astype(np.float32)
+    x = rng.uniform(-spread, 1 + spread, n).astype(np.float32)
+    y = rng.uniform(-spread, 1 + spread, n).astype(np.float32)
+    z = lv[rng.integers(0, len(lv), n)]
+    return depth, x, y, z
+
+
+@pytest.mark.parametrize("n", [0, 1, 3, 1023, 1024, 1025, 4097, 100003])
+def test_ragged_sizes(api, n):
+    rng = np.random.default_rng(n)
+    depth, x, y, z = _random_case(rng, 64, 48, n)
+    if n == 0:
+        vis, cod = run_gpu(api, depth, x, y, z, orc.MODE_FILTER)
+        assert vis.shape == (0,)
+        return
+    check_both(api, depth, x, y, z, "n=%d" % n)
+
+
+@pytest.mark.parametrize("w,h", [(1, 1), (1, 9), (9, 1), (2, 2), (3, 700), (1000, 3), (257, 129)])
+def test_degenerate_and_odd_maps(api, w, h):
+    rng = np.random.default_rng(w * 1000 + h)
+    depth, x, y, z = _random_case(rng, w, h, 5000)
+    check_both(api, depth, x, y, z, "%dx%d" % (w, h))
+
+
+def test_out_of_range_and_nan_coordinates(api):
+    """Clamp-to-edge addressing; a NaN coordinate maps to texel 0 on both sides."""
+    rng = np.random.default_rng(5)
+    depth, x, y, z = _random_case(rng, 40, 40, 20000, spread=0.3)
+    x[::97] = np.nan
+    y[::89] = -np.inf
+    x[::83] = np.inf
+    check_both(api, depth, x, y, z, "out-of-range")
+
+
+@pytest.mark.parametrize("max_dist", [1, 2, 5, 16, 64, 255])
+def test_max_dist(api, max_dist):
+    import rbsm_scenes as sc
+    f = sc.config1(1)
+    check_both(api, f.depth, f.x, f.y, f.z, "max_dist=%d" % max_dist, max_dist=max_dist)
+
+
+def test_pitched_map_and_unaligned_planes(api):
+    """A map whose rows are padded (pitch > width) and fragment planes that
+    start 4 bytes past a 16-byte boundary (scalar path) give the same answers."""
+    import rbsm_scenes as sc
+    f = sc.config1(2)
+    h, w = f.depth.shape
+    big = torch.full((h, w + 13), 7.0, dtype=torch.float32, device="cuda")
+    big[:, :w] = dev(f.depth)
+    pitched = big[:, :w]
+    assert pitched.stride(0) == w + 13
+    n = f.n
+    planes = []
+    for a in (f.x, f.y, f.z):
+        buf = torch.empty(n + 1, dtype=torch.float32, device="cuda")
+        buf[1:] = dev(a)
+        planes.append(buf[1:])
+    assert planes[0].data_ptr() % 16 != 0
+    for mode in (orc.MODE_SILHOUETTE, orc.MODE_FILTER):
+        ref = orc.evaluate(f.depth, f.x, f.y, f.z, mode)
+        vis, cod = run_gpu(api, pitched, *planes, mode)
+        assert_parity(vis, cod, ref, mode, "pitched/unaligned")
+        vis2, _ = run_gpu(api, f.depth, f.x, f.y, f.z, mode, codes=False)
+        assert np.array_equal(vis, vis2)
+
+
+def test_equal_depth_ties(api):
+    """Eq. 1 is strict: a fragment at exactly the stored depth is lit."""
+    rng = np.random.default_rng(9)
+    depth, x, y, z = _random_case(rng, 33, 31, 50000, levels=(0.5, 0.5000001, 1.0))
+    check_both(api, depth, x, y, z, "ties")
+
+
+def test_host_buffers_roundtrip(api):
+    """CPU (host) tensors go through the same kernels and give the same answers."""
+    import rbsm_scenes as sc
+    f = sc.config1(0)
+    args = [torch.from_numpy(a).pin_memory() for a in (f.depth, f.x, f.y, f.z)]
+    vis_h, cod_h = api.rsmss_filter(*args, codes=True)
+    ref = orc.evaluate(f.depth, f.x, f.y, f.z, orc.MODE_FILTER)
+    assert_parity(vis_h.numpy(), cod_h.numpy().view(np.uint16), ref, orc.MODE_FILTER, "host")
