@@ -24,7 +24,7 @@ def _check_plane(name, t, n=None):
         raise TypeError("%s must be a 1-D float32 tensor" % name)
     if not t.is_cuda:
         raise TypeError("%s must be a CUDA tensor" % name)
-    if t.stride(0) != 1:
+    if t.numel() > 1 and t.stride(0) != 1:
         raise ValueError("%s must be contiguous" % name)
     if n is not None and t.shape[0] != n:
         raise ValueError("%s has %d elements, expected %d" % (name, t.shape[0], n))
