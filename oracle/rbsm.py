@@ -29,6 +29,11 @@ def _load():
             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
             ctypes.c_int32, ctypes.c_int32,
             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.oracle_features.restype = ctypes.c_int
+        lib.oracle_features.argtypes = [
+            ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         _lib = lib
     return _lib
 
@@ -67,3 +72,20 @@ def evaluate(depth, x, y, z, mode, max_dist=MAXDIST, want_rd=False, want_nrd=Fal
     if want_nrd:
         out["nrd"] = nrd
     return out
+
+
+def features(depth, x, y, z):
+    """Surrogate features of every fragment: 25-bit 5x5 shadow-test pattern
+    (uint32), in-texel offsets fx, fy and depth gap (float32)."""
+    lib = _load()
+    depth = np.ascontiguousarray(depth, dtype=np.float32)
+    x, y, z = (np.ascontiguousarray(a, dtype=np.float32) for a in (x, y, z))
+    n = x.shape[0]
+    h, w = depth.shape
+    bits = np.empty(n, np.uint32)
+    fx, fy, gap = (np.empty(n, np.float32) for _ in range(3))
+    rc = lib.oracle_features(_ptr(depth), w, h, w, _ptr(x), _ptr(y), _ptr(z), n,
+                             _ptr(bits), _ptr(fx), _ptr(fy), _ptr(gap))
+    if rc != 0:
+        raise ValueError("oracle_features rejected its arguments (rc=%d)" % rc)
+    return {"bits": bits, "fx": fx, "fy": fy, "gap": gap}

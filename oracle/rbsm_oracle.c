@@ -300,3 +300,49 @@ int oracle_rbsm_eval(const float *depth, int32_t width, int32_t height, int64_t 
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Features of the learned penumbra surrogate.  Not in the paper: this
+ * project's surrogate of the Listing 5 (RSMSS) answer for edge fragments
+ * reads, per fragment,
+ *   bits: the shadow tests (Eq. 1, with the fragment's depth) of the 5x5
+ *         texels around its texel (clamp to edge, R2); texel (i+dx, j+dy)
+ *         sets bit (dy+2)*5 + (dx+2) when it is lit;
+ *   fx, fy: the in-texel offsets of R1;
+ *   gap:  the fragment's depth minus the smallest depth stored in the 5x5
+ *         window (float32 subtraction), the blocker-receiver depth gap.
+ * Returns 0, or -1 on invalid arguments.
+ */
+int oracle_features(const float *depth, int32_t width, int32_t height, int64_t pitch,
+                    const float *px, const float *py, const float *pz, int64_t n,
+                    uint32_t *bits, float *fx_out, float *fy_out, float *gap_out)
+{
+    if (!depth || width < 1 || height < 1 || pitch < width || n < 0)
+        return -1;
+    if (n > 0 && (!px || !py || !pz || !bits || !fx_out || !fy_out || !gap_out))
+        return -1;
+    sm_t sm = {depth, width, height, pitch};
+    for (int64_t t = 0; t < n; ++t) {
+        float u = px[t] * (float)width;
+        float v = py[t] * (float)height;
+        float fu = floorf(u), fv = floorf(v);
+        int64_t i = (int64_t)fminf(fmaxf(fu, 0.0f), (float)(width - 1));
+        int64_t j = (int64_t)fminf(fmaxf(fv, 0.0f), (float)(height - 1));
+        uint32_t b = 0;
+        float zmin = sm_depth(&sm, i, j);
+        for (int dy = -2; dy <= 2; ++dy) {
+            for (int dx = -2; dx <= 2; ++dx) {
+                float zt = sm_depth(&sm, i + dx, j + dy);
+                if (shadow_test(pz[t], zt))
+                    b |= 1u << ((dy + 2) * 5 + (dx + 2));
+                if (zt < zmin)
+                    zmin = zt;
+            }
+        }
+        bits[t] = b;
+        fx_out[t] = u - fu;
+        fy_out[t] = v - fv;
+        gap_out[t] = pz[t] - zmin;
+    }
+    return 0;
+}

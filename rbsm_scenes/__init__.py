@@ -380,3 +380,22 @@ class Config3:
     @property
     def n(self):
         return sum(j.x.shape[0] for j in self.jobs)
+
+
+# ------------------------------------------------------ surrogate weights --
+
+MLP_IN, MLP_HID, MLP_OUT = 32, 64, 2
+
+
+def mlp_init(seed):
+    """Seeded initial weights of the 32-64-64-2 surrogate network (He-normal
+    weights, zero biases), float32; both the GPU trainer and the oracle start
+    from these arrays."""
+    g = np.random.Generator(np.random.PCG64(7000 + seed))
+
+    def he(fan_in, shape):
+        return (g.standard_normal(shape) * math.sqrt(2.0 / fan_in)).astype(np.float32)
+
+    return {"W1": he(28, (MLP_IN, MLP_HID)), "b1": np.zeros(MLP_HID, np.float32),
+            "W2": he(MLP_HID, (MLP_HID, MLP_HID)), "b2": np.zeros(MLP_HID, np.float32),
+            "W3": he(MLP_HID, (MLP_HID, MLP_OUT)) * np.float32(0.1), "b3": np.array([0.5, 0.05], np.float32)}
