@@ -51,6 +51,8 @@ def parse_args(argv=None):
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--skip-e2e", action="store_true", help="profiling runs only")
     p.add_argument("--skip-cpu", action="store_true", help="profiling runs only")
+    p.add_argument("--skip-learned", action="store_true", help="profiling runs only")
+    p.add_argument("--guard-tau", type=float, default=0.05, help="surrogate guard (largest accepted error estimate)")
     p.add_argument("--tile-threads", type=int, default=0)
     p.add_argument("--ctas-per-sm", type=int, default=0)
     return p.parse_args(argv)
@@ -349,6 +351,10 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": world * frames * n_frag / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
 
+    learned = None
+    if not args.skip_learned:
+        learned = compare_learned(api, maps, xyz, frames, n_frag, args, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         cpu = oracle_throughput(host)
@@ -373,6 +379,7 @@ def run_ours(args, rank, world, local_rank):
                      "mean_launch_ms": mean_launch_ms, "min_launch_ms": min(launch_ms)},
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "learned": learned,
         "gpu_launches": args.steps,
         "clocks": clocks,
         "edge": {"unique_texels_per_frame": statistics.mean(h["U"] for h in host)},
@@ -382,6 +389,70 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- learned --
+
+CHECKPOINT = os.path.join(ROOT, "paper_1711_07793_gb300", "weights", "surrogate_c4.npz")
+
+
+def compare_learned(api, maps, xyz, frames, n_frag, args, stream):
+    """Plain RSMSS against the surrogate with its guard, both batched over
+    the same frames in one persistent launch per step (filtering mode): time
+    per step, the surrogate's share of edge fragments, and the error of the
+    learned answers against the plain ones (over every fragment and over the
+    fragments the surrogate answered)."""
+    import torch
+    from paper_1711_07793_gb300.surrogate import Surrogate
+    if not os.path.exists(CHECKPOINT):
+        return {"unavailable": "no surrogate checkpoint (run python -m paper_1711_07793_gb300.train_surrogate)"}
+    net = Surrogate.from_checkpoint(CHECKPOINT)
+    plain_jobs = [api.Job(k, xyz[k][0], xyz[k][1], xyz[k][2], mode=2) for k in range(frames)]
+    net_jobs = [api.Job(k, xyz[k][0], xyz[k][1], xyz[k][2], mode=2, codes=True) for k in range(frames)]
+    plain = api.Batch(maps, plain_jobs, tile_threads=args.tile_threads, ctas_per_sm=args.ctas_per_sm)
+    learned = api.Batch(maps, net_jobs, tile_threads=args.tile_threads, ctas_per_sm=args.ctas_per_sm,
+                        surrogate=net, guard_tau=args.guard_tau)
+    steps = max(3, min(args.steps, 200))
+
+    def timed(batch):
+        for _ in range(3):
+            api.rbsm_batch_run(batch)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            api.rbsm_batch_run(batch)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    ms_plain = timed(plain)
+    ms_learned = timed(learned)
+    acc, fb = api.rbsm_batch_surrogate_counts(learned)
+    errs, errs_net = [], []
+    for pj, lj in zip(plain_jobs, net_jobs):
+        d = (lj.vis_filter - pj.vis_filter).abs()
+        errs.append(d)
+        answered = ((lj.codes.to(torch.int32) >> 10) & 1) == 1
+        errs_net.append(d[answered])
+    d = torch.cat(errs).double()
+    dn = torch.cat(errs_net).double()
+    def q(t, p):
+        if t.numel() == 0:
+            return None
+        k = max(1, int(round(p * t.numel())))
+        return float(torch.kthvalue(t.cpu(), k).values)
+    fps = lambda ms: frames * n_frag / (ms * 1e-3) / 1e9
+    return {"metric": "Gfragments/s RSMSS (filtering) visibility, same frames, one batched launch per step",
+            "plain": {"value": fps(ms_plain), "ms_per_step": ms_plain},
+            "learned": {"value": fps(ms_learned), "ms_per_step": ms_learned, "guard_tau": args.guard_tau},
+            "speedup": ms_plain / ms_learned,
+            "edge_fragments": acc + fb, "surrogate_answers": acc, "fallbacks": fb,
+            "fallback_frac": fb / max(1, acc + fb),
+            "error_vs_plain_all": {"mean": float(d.mean()), "p99": q(d, 0.99), "max": float(d.max())},
+            "error_vs_plain_answered": {"mean": float(dn.mean()) if dn.numel() else None, "p99": q(dn, 0.99),
+                                        "max": float(dn.max()) if dn.numel() else None},
+            "checkpoint": {k: net.header.get(k) for k in ("samples", "epochs", "data", "loss_per_epoch")}}
 
 
 # -------------------------------------------------------------- reference --

@@ -142,8 +142,19 @@ typedef struct {
     const rbsm_job *jobs;          /* host array of n_jobs descriptors */
     int32_t n_jobs;                /* 1..RBSM_BATCH_MAX_JOBS */
     rbsm_params params;
-    int32_t tile_threads;          /* CTA size: 128, 256 or 512; 0 = default 256 */
-    int32_t ctas_per_sm;           /* persistent CTAs per SM, 1..8; 0 = occupancy limit */
+    int32_t tile_threads;          /* CTA size: 128, 256 or 512 threads; 0 = default 256 */
+    int32_t ctas_per_sm;           /* persistent CTAs per SM, 1..8; 0 = occupancy limit.  At
+                                    * 256 threads, 5 or 6 select a variant compiled for 5 or
+                                    * 6 CTAs per SM (fewer registers per thread) */
+    /* Learned penumbra (not in the paper): NULL = exact everywhere.  Given a
+     * network state block (rbsm_mlp_state_bytes), FILTER-mode jobs answer
+     * their edge fragments with the surrogate wherever its own error
+     * estimate is <= guard_tau and fall back to the exact walk elsewhere;
+     * shadow tests, discontinuity codes and off-edge answers stay exact, and
+     * SILHOUETTE / BOTH jobs are not touched.  A surrogate answer's code has
+     * bit 10 set and no end counts (bits 5-9 clear). */
+    const void *surrogate;
+    float guard_tau;
 } rbsm_batch;
 
 /*
@@ -155,7 +166,8 @@ int rbsm_batch_workspace_size(const rbsm_batch *batch, size_t *bytes);
 
 /*
  * Enqueue one batched launch: a memset of the workspace followed by one
- * persistent kernel whose CTAs take (job, tile) items from an atomic counter.
+ * persistent kernel whose warps take chunks of 1024 fragments (8 tiles of
+ * 128, in job order) from an atomic counter in the workspace.
  * The descriptors are copied into the launch parameters, so the host arrays
  * may be reused as soon as the call returns.  Errors: RBSM_ERR_ARG as for
  * rbsm_visibility applied to every map and job, or a map index out of range;
@@ -165,11 +177,111 @@ int rbsm_batch_workspace_size(const rbsm_batch *batch, size_t *bytes);
 int rbsm_batch_run(const rbsm_batch *batch, void *workspace, size_t workspace_bytes, void *stream);
 
 /*
+ * CUDA graph of one batched launch (the workspace memset and the persistent
+ * kernel), built once and replayed with one cudaGraphLaunch per frame.  The
+ * graph captures the descriptors, the device pointers and the workspace as
+ * they are at creation: replaying it reads whatever those buffers then hold.
+ * Creation allocates the graph (host and driver resources) and must not run
+ * while the calling thread captures a stream; launching allocates nothing.
+ * Errors as for rbsm_batch_run; rbsm_batch_graph_launch returns RBSM_ERR_ARG
+ * for a NULL graph and RBSM_ERR_CUDA when the launch fails.
+ */
+typedef struct rbsm_graph_s *rbsm_graph;
+int rbsm_batch_graph_create(const rbsm_batch *batch, void *workspace, size_t workspace_bytes,
+                            rbsm_graph *graph);
+int rbsm_batch_graph_launch(rbsm_graph graph, void *stream);
+int rbsm_batch_graph_destroy(rbsm_graph graph);
+
+/*
+ * Autotuner of the batched launch shape.  Times 8 candidate (CTA size,
+ * CTAs per SM) pairs: 128 threads at its occupancy limit; 256 threads at 2,
+ * 3, 4 (occupancy limit), 5 and 6 CTAs per SM; 512 threads at 1 and 2.
+ * Every warp works on its own 128-fragment tiles whatever the CTA size.
+ * Each candidate gets `repeats` launches
+ * each after one warm-up, on `stream`, and returns the fastest in *best.
+ * It writes the batch's outputs (the answers stay correct) and waits for
+ * the stream (cudaEventSynchronize): a set-up call, not for a frame loop.
+ */
+typedef struct {
+    int32_t tile_threads;
+    int32_t ctas_per_sm;           /* 0 = occupancy limit */
+    float ms;                      /* mean time per launch of the winner */
+    int32_t candidates;            /* shapes timed */
+} rbsm_tuning;
+int rbsm_batch_autotune(const rbsm_batch *batch, void *workspace, size_t workspace_bytes, void *stream,
+                        int32_t repeats, rbsm_tuning *best);
+
+/*
+ * After the stream has completed a batch: the number of edge fragments the
+ * surrogate answered and the number it handed to the exact walk (guard
+ * tripped) in its last launch (synchronous device-to-host copy).
+ */
+int rbsm_batch_surrogate_counts(const void *workspace, uint64_t *accepted, uint64_t *fallback);
+
+/*
  * After the stream has completed a batch: read its device status word
  * (synchronously, with a device-to-host copy) and return RBSM_OK or the
  * RBSM_ERR_* code the kernel recorded.
  */
 int rbsm_batch_status(const void *workspace, int *status);
+
+/*
+ * Learned penumbra surrogate (not in the paper; this library's addition).
+ * A 32-64-64-2 perceptron estimates the Listing 5 answer of an edge
+ * fragment from its 5x5 shadow-test pattern (bit (dy+2)*5 + (dx+2) set when
+ * texel (i+dx, j+dy) is lit), its in-texel offsets and the depth gap to the
+ * nearest blocker of the window, plus an estimate of its own absolute
+ * error.  BF16 weights and activations, FP32 accumulation (tensor cores).
+ *
+ * The state block (device, caller-allocated, 256-byte aligned,
+ * rbsm_mlp_state_bytes() bytes) holds the FP32 master parameters, their
+ * gradient, the Adam moments, BF16 weight copies and a loss accumulator.
+ * The FP32 parameter vector has RBSM_MLP_PARAMS floats in the order
+ * W1 (32 x 64, row-major (in, out)), b1 (64), W2 (64 x 64), b2 (64),
+ * W3 (64 x 2), b3 (2).
+ */
+#define RBSM_MLP_PARAMS 6402
+
+/* One training sample: features of an edge fragment and its exact RSMSS answer. */
+typedef struct {
+    uint32_t bits;                 /* 25-bit 5x5 shadow-test pattern */
+    float fx, fy;                  /* in-texel offsets */
+    float gap;                     /* fragment depth - nearest blocker depth in the window */
+    float label;                   /* Listing 5 visibility */
+} rbsm_sample;
+
+size_t rbsm_mlp_state_bytes(void);
+
+/* Copy n = RBSM_MLP_PARAMS host floats in (stream-ordered; the host array
+ * must stay valid until the stream reaches the copy), zero the gradient,
+ * the Adam moments and the loss, build the BF16 copies. */
+int rbsm_mlp_load(void *state, const float *params_host, void *stream);
+
+/* Copy the FP32 master parameters out to host memory (stream-ordered). */
+int rbsm_mlp_store(const void *state, float *params_host, void *stream);
+
+/* Append every edge fragment of a fragment set (filtering mode) as a
+ * training sample at the device counter *counter (which the caller zeroes
+ * once); samples past `capacity` are counted but not written. */
+int rbsm_mlp_dataset(const rbsm_map *map, const rbsm_frags *frags, const rbsm_params *params,
+                     rbsm_sample *samples, int64_t capacity, unsigned long long *counter, void *stream);
+
+/* Accumulate the loss gradient of one minibatch (samples[order[0..batch)])
+ * into the state: loss = mean (y0 - t)^2 + mean (y1 - |clamp(y0,0,1) - t|)^2,
+ * the second target held constant. */
+int rbsm_mlp_grad(void *state, const rbsm_sample *samples, const int32_t *order, int32_t batch, void *stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr;
+ * `step` counts from 1; clears the gradient. */
+int rbsm_mlp_adam(void *state, int32_t step, float lr, void *stream);
+
+/* Synchronously read the accumulated gradient (RBSM_MLP_PARAMS floats) and/or
+ * the loss sum since the last reset (either pointer may be NULL). */
+int rbsm_mlp_read(const void *state, float *grad_host, float *loss_host, void *stream);
+int rbsm_mlp_reset_loss(void *state, void *stream);
+
+/* Network outputs (n x 2 floats: estimate, error estimate) of n samples. */
+int rbsm_mlp_forward(const void *state, const rbsm_sample *samples, int64_t n, float *out, void *stream);
 
 /* Text for a return code. */
 const char *rbsm_status_string(int code);

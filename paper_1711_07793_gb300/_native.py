@@ -50,7 +50,21 @@ class rbsm_batch(ctypes.Structure):
     _fields_ = [("maps", ctypes.POINTER(rbsm_map)), ("n_maps", ctypes.c_int32),
                 ("jobs", ctypes.POINTER(rbsm_job)), ("n_jobs", ctypes.c_int32),
                 ("params", rbsm_params), ("tile_threads", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("surrogate", ctypes.c_void_p),
+                ("guard_tau", ctypes.c_float)]
+
+
+class rbsm_sample(ctypes.Structure):
+    _fields_ = [("bits", ctypes.c_uint32), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("gap", ctypes.c_float), ("label", ctypes.c_float)]
+
+
+RBSM_MLP_PARAMS = 6402
+
+
+class rbsm_tuning(ctypes.Structure):
+    _fields_ = [("tile_threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("ms", ctypes.c_float), ("candidates", ctypes.c_int32)]
 
 
 class RBSMError(RuntimeError):
@@ -77,8 +91,35 @@ def _declare(lib):
     lib.rbsm_batch_workspace_size.argtypes = [_P(rbsm_batch), _P(ctypes.c_size_t)]
     lib.rbsm_batch_run.restype = i32
     lib.rbsm_batch_run.argtypes = [_P(rbsm_batch), vp, ctypes.c_size_t, vp]
+    lib.rbsm_batch_graph_create.restype = i32
+    lib.rbsm_batch_graph_create.argtypes = [_P(rbsm_batch), vp, ctypes.c_size_t, _P(vp)]
+    lib.rbsm_batch_graph_launch.restype = i32
+    lib.rbsm_batch_graph_launch.argtypes = [vp, vp]
+    lib.rbsm_batch_graph_destroy.restype = i32
+    lib.rbsm_batch_graph_destroy.argtypes = [vp]
+    lib.rbsm_batch_autotune.restype = i32
+    lib.rbsm_batch_autotune.argtypes = [_P(rbsm_batch), vp, ctypes.c_size_t, vp, ctypes.c_int32, _P(rbsm_tuning)]
     lib.rbsm_batch_status.restype = i32
     lib.rbsm_batch_status.argtypes = [vp, _P(ctypes.c_int)]
+    lib.rbsm_batch_surrogate_counts.restype = i32
+    lib.rbsm_batch_surrogate_counts.argtypes = [vp, _P(ctypes.c_uint64), _P(ctypes.c_uint64)]
+    lib.rbsm_mlp_state_bytes.restype = ctypes.c_size_t
+    lib.rbsm_mlp_state_bytes.argtypes = []
+    for name in ("rbsm_mlp_load", "rbsm_mlp_store"):
+        getattr(lib, name).restype = i32
+        getattr(lib, name).argtypes = [vp, vp, vp]
+    lib.rbsm_mlp_dataset.restype = i32
+    lib.rbsm_mlp_dataset.argtypes = [_P(rbsm_map), _P(rbsm_frags), _P(rbsm_params), vp, ctypes.c_int64, vp, vp]
+    lib.rbsm_mlp_grad.restype = i32
+    lib.rbsm_mlp_grad.argtypes = [vp, vp, vp, ctypes.c_int32, vp]
+    lib.rbsm_mlp_adam.restype = i32
+    lib.rbsm_mlp_adam.argtypes = [vp, ctypes.c_int32, ctypes.c_float, vp]
+    lib.rbsm_mlp_read.restype = i32
+    lib.rbsm_mlp_read.argtypes = [vp, vp, vp, vp]
+    lib.rbsm_mlp_reset_loss.restype = i32
+    lib.rbsm_mlp_reset_loss.argtypes = [vp, vp]
+    lib.rbsm_mlp_forward.restype = i32
+    lib.rbsm_mlp_forward.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
     lib.rbsm_status_string.restype = ctypes.c_char_p
     lib.rbsm_status_string.argtypes = [i32]
     lib.rbsm_last_cuda_error.restype = i32

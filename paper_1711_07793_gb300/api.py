@@ -8,6 +8,8 @@ evaluated there and the answers copied back (the host-buffer path); every
 step of the method runs in the library's kernels either way.
 """
 import ctypes
+import json
+import os
 
 import torch
 
@@ -130,12 +132,16 @@ class Job:
 class Batch:
     """Descriptor arrays of a batched launch, kept alive with their tensors."""
 
-    def __init__(self, maps, jobs, max_dist=N.RBSM_MAXDIST_DEFAULT, tile_threads=0, ctas_per_sm=0):
+    def __init__(self, maps, jobs, max_dist=N.RBSM_MAXDIST_DEFAULT, tile_threads=0, ctas_per_sm=0,
+                 surrogate=None, guard_tau=0.0):
         self.maps, self.jobs = list(maps), list(jobs)
+        self.surrogate = surrogate
         self._maps = (N.rbsm_map * len(self.maps))(*[map_desc(m) for m in self.maps])
         self._jobs = (N.rbsm_job * len(self.jobs))(*[j.desc() for j in self.jobs])
         self.desc = N.rbsm_batch(self._maps, len(self.maps), self._jobs, len(self.jobs),
-                                 _params(max_dist), int(tile_threads), int(ctas_per_sm))
+                                 _params(max_dist), int(tile_threads), int(ctas_per_sm),
+                                 surrogate.state.data_ptr() if surrogate is not None else None,
+                                 float(guard_tau))
         size = ctypes.c_size_t(0)
         N.check("rbsm_batch_workspace_size", N.lib().rbsm_batch_workspace_size(ctypes.byref(self.desc),
                                                                               ctypes.byref(size)))
@@ -163,3 +169,84 @@ def rbsm_batch_status(batch):
     N.check("rbsm_batch_status", N.lib().rbsm_batch_status(ctypes.c_void_p(batch.workspace.data_ptr()),
                                                            ctypes.byref(st)))
     return st.value
+
+
+class BatchGraph:
+    """A CUDA graph of one batched launch of `batch` (rbsm_batch_graph_*):
+    built once, replayed by launch().  It binds the batch's tensors as they
+    are now; keep `batch` alive while the graph is used."""
+
+    def __init__(self, batch):
+        self.batch = batch
+        h = ctypes.c_void_p(0)
+        N.check("rbsm_batch_graph_create",
+                N.lib().rbsm_batch_graph_create(ctypes.byref(batch.desc), ctypes.c_void_p(batch.workspace.data_ptr()),
+                                                batch.workspace_bytes, ctypes.byref(h)))
+        self.handle = h
+
+    def launch(self, stream=None):
+        N.check("rbsm_batch_graph_launch", N.lib().rbsm_batch_graph_launch(self.handle, _stream_handle(stream)))
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            N.check("rbsm_batch_graph_destroy", N.lib().rbsm_batch_graph_destroy(self.handle))
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_signature(batch):
+    """Key of a batch for the autotuner cache: device, map sizes, job sizes."""
+    name = torch.cuda.get_device_name(batch.jobs[0].x.device)
+    maps = [tuple(m.shape) for m in batch.maps]
+    jobs = [(j.map_index, j.mode, int(j.x.shape[0]), j.codes is not None) for j in batch.jobs]
+    return json.dumps([name, maps, jobs])
+
+
+TUNE_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune_cache.json")
+
+
+def rbsm_batch_autotune(batch, repeats=3, stream=None, cache=TUNE_CACHE):
+    """Pick the batched launch shape by timing the candidates on this GPU
+    (rbsm_batch_autotune), remember it per batch signature in `cache`
+    (None: no file), apply it to `batch` and return the rbsm_tuning fields."""
+    key = batch_signature(batch)
+    table = {}
+    if cache and os.path.exists(cache):
+        try:
+            with open(cache) as f:
+                table = json.load(f)
+        except (OSError, ValueError):
+            table = {}
+    if key in table:
+        hit = dict(table[key], cached=True)
+        batch.set_launch(hit["tile_threads"], hit["ctas_per_sm"])
+        return hit
+    t = N.rbsm_tuning()
+    N.check("rbsm_batch_autotune",
+            N.lib().rbsm_batch_autotune(ctypes.byref(batch.desc), ctypes.c_void_p(batch.workspace.data_ptr()),
+                                        batch.workspace_bytes, _stream_handle(stream), int(repeats),
+                                        ctypes.byref(t)))
+    res = {"tile_threads": t.tile_threads, "ctas_per_sm": t.ctas_per_sm, "ms": t.ms, "candidates": t.candidates}
+    batch.set_launch(t.tile_threads, t.ctas_per_sm)
+    if cache:
+        table[key] = res
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        tmp = cache + ".tmp%d" % os.getpid()
+        with open(tmp, "w") as f:
+            json.dump(table, f, indent=1)
+        os.replace(tmp, cache)
+    return dict(res, cached=False)
+
+
+def rbsm_batch_surrogate_counts(batch):
+    """(surrogate answers, guard fallbacks) of the last completed launch."""
+    a, f = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    N.check("rbsm_batch_surrogate_counts",
+            N.lib().rbsm_batch_surrogate_counts(ctypes.c_void_p(batch.workspace.data_ptr()), ctypes.byref(a),
+                                                ctypes.byref(f)))
+    return a.value, f.value

@@ -1,19 +1,15 @@
 // Device-side steps of the RBSM per-fragment path for sm_103a.
 //
-// One CTA owns a tile of kTile consecutive fragments at a time:
-//   1. load the tile's x/y/z planes with 16-byte vector loads (or coalesced
-//      scalar loads for unaligned planes) into shared memory and registers;
-//   2. classify every fragment: shadow test of its texel (Eq. 1) and of its
-//      four neighbours, discontinuity directions (Eqs. 2-4).  Fragments off
-//      the shadow edge are finished here (plain shadow test, Listing 1);
-//      edge fragments are appended to a per-CTA queue with one warp-aggregated
-//      atomic per warp;
-//   3. the whole CTA drains the queue with converged lanes: the four edge
-//      walks (Listing 3), the normalisation (Eq. 5) and the optimized
-//      visibility (Listing 4 and/or Listing 5);
-//   4. store the tile's answers with vector stores.
-// Compacting edge fragments keeps their long, data-dependent walks from
-// idling the 31 other lanes of a warp whose fragments are all off the edge.
+// Per fragment: texel and in-texel offsets (float32, as the paper's GLSL),
+// shadow test of the texel and of its four neighbours (Eq. 1, Eq. 2),
+// discontinuity directions (Eqs. 3-4).  Fragments off the shadow edge are
+// finished there (the plain shadow test, Listing 1).  Edge fragments walk the
+// edge (Listing 3), normalise their position (Eq. 5) and take the optimized
+// visibility (Listing 4 and/or Listing 5).
+//
+// Work unit: a warp tile of 128 consecutive fragments (below).  Edge
+// fragments of a tile are compacted so that their long, data-dependent walks
+// run on adjacent lanes instead of serialising all four fragments of a lane.
 #pragma once
 
 #include <cstdint>
@@ -62,34 +58,45 @@ __device__ __forceinline__ void texel_coord(float x, int size, int &t, float &f)
 // with the fragment.  Along x only the +-y directions can be shared: the
 // walk's texel has the same result as the texel it came from (so no shared
 // direction back along the walk), and the fragment has no discontinuity in
-// the walking direction (else the first step ends the walk).  Returns +k for
-// an end found at step k, -k for a texel that left the edge, -(max_dist+1)
-// when all steps continued.
+// the walking direction (else the first step ends the walk).  Both facts
+// hold with clamp-to-edge addressing too.  Returns +k for an end found at
+// step k, -k for a texel that left the edge, -(max_dist+1) when all steps
+// continued.  The three rows the walk reads are fixed: their addresses are
+// formed once.
 __device__ __forceinline__ int walk_x(const MapDev &m, int i, int j, float pz, int s0,
                                       bool up, bool down, int di, int max_dist)
 {
+    const float *row = m.depth + (long long)j * m.pitch;
+    const float *row_up = m.depth + (long long)min(j + 1, m.height - 1) * m.pitch;
+    const float *row_dn = m.depth + (long long)max(j - 1, 0) * m.pitch;
+    const int last = m.width - 1;
     for (int k = 1; k <= max_dist; ++k) {
-        int c = i + k * di;
-        if (shadow_test(pz, texel(m, c, j)) != s0)
+        const int c = min(max(i + k * di, 0), last);
+        if (shadow_test(pz, __ldg(row + c)) != s0)
             return k;
-        bool keep = (up && shadow_test(pz, texel(m, c, j + 1)) != s0) ||
-                    (down && shadow_test(pz, texel(m, c, j - 1)) != s0);
+        const bool keep = (up && shadow_test(pz, __ldg(row_up + c)) != s0) ||
+                          (down && shadow_test(pz, __ldg(row_dn + c)) != s0);
         if (!keep)
             return -k;
     }
     return -(max_dist + 1);
 }
 
-// Listing 3 along y (only the left/right directions can be shared).
+// Listing 3 along y (only the left/right directions can be shared); the
+// three columns are fixed.
 __device__ __forceinline__ int walk_y(const MapDev &m, int i, int j, float pz, int s0,
                                       bool left, bool right, int dj, int max_dist)
 {
+    const float *col = m.depth + i;
+    const float *col_l = m.depth + max(i - 1, 0);
+    const float *col_r = m.depth + min(i + 1, m.width - 1);
+    const int last = m.height - 1;
     for (int k = 1; k <= max_dist; ++k) {
-        int r = j + k * dj;
-        if (shadow_test(pz, texel(m, i, r)) != s0)
+        const long long off = (long long)min(max(j + k * dj, 0), last) * m.pitch;
+        if (shadow_test(pz, __ldg(col + off)) != s0)
             return k;
-        bool keep = (left && shadow_test(pz, texel(m, i - 1, r)) != s0) ||
-                    (right && shadow_test(pz, texel(m, i + 1, r)) != s0);
+        const bool keep = (left && shadow_test(pz, __ldg(col_l + off)) != s0) ||
+                          (right && shadow_test(pz, __ldg(col_r + off)) != s0);
         if (!keep)
             return -k;
     }
@@ -145,6 +152,41 @@ __device__ __forceinline__ float filter(bool dx3, bool dy3, int dz, int ex, int 
     return v > 1.0f ? 1.0f : v;
 }
 
+// Features of the learned surrogate (this project's addition; not in the paper).
+// 5x5 shadow-test pattern and nearest blocker depth around texel (i, j)
+// (clamp to edge): bit (dy+2)*5 + (dx+2) is set when texel (i+dx, j+dy) is
+// lit for depth pz.
+__device__ __forceinline__ void window5(const MapDev &m, int i, int j, float pz, uint32_t &bits, float &zmin)
+{
+    bits = 0;
+    zmin = texel(m, i, j);
+    int cols[5];
+#pragma unroll
+    for (int d = 0; d < 5; ++d)
+        cols[d] = min(max(i + d - 2, 0), m.width - 1);
+#pragma unroll
+    for (int dy = 0; dy < 5; ++dy) {
+        const float *row = m.depth + (long long)min(max(j + dy - 2, 0), m.height - 1) * m.pitch;
+#pragma unroll
+        for (int dx = 0; dx < 5; ++dx) {
+            const float zt = __ldg(row + cols[dx]);
+            bits |= (uint32_t)shadow_test(pz, zt) << (dy * 5 + dx);
+            zmin = fminf(zmin, zt);
+        }
+    }
+}
+
+__device__ __forceinline__ void fragment_features(const MapDev &m, float x, float y, float pz, uint32_t &bits,
+                                                  float &fx, float &fy, float &gap)
+{
+    int i, j;
+    texel_coord(x, m.width, i, fx);
+    texel_coord(y, m.height, j, fy);
+    float zmin;
+    window5(m, i, j, pz, bits, zmin);
+    gap = __fsub_rn(pz, zmin);
+}
+
 // Result of one fragment.
 struct FragResult {
     float sil;
@@ -155,7 +197,8 @@ struct FragResult {
 // Steps 1-2 for one fragment: texel, shadow test, four-neighbourhood.
 // Returns true when the fragment needs the edge walk for this mode; packs
 // s0 and the four directions into `bits` (bit 0 = s0, bits 1-4 = left,
-// right, +y, -y).
+// right, +y, -y).  Away from the border the four neighbours are plain
+// offsets (+-1, +-pitch) of the centre texel's address.
 template <int MODE, bool CODES>
 __device__ __forceinline__ bool classify(const MapDev &m, float x, float y, float pz,
                                          FragResult &r, uint32_t &bits)
@@ -164,7 +207,8 @@ __device__ __forceinline__ bool classify(const MapDev &m, float x, float y, floa
     float fx, fy;
     texel_coord(x, m.width, i, fx);
     texel_coord(y, m.height, j, fy);
-    int s0 = shadow_test(pz, texel(m, i, j));
+    const float *c = m.depth + (long long)j * m.pitch + i;
+    const int s0 = shadow_test(pz, __ldg(c));
     // Listing 1: in silhouette recovery a shadowed fragment stays shadowed and
     // needs no neighbourhood (unless codes are requested).
     if (MODE == 1 && !CODES && s0 == 0) {
@@ -173,17 +217,29 @@ __device__ __forceinline__ bool classify(const MapDev &m, float x, float y, floa
         bits = 0;
         return false;
     }
-    int dl = shadow_test(pz, texel(m, i - 1, j)) != s0;
-    int dr = shadow_test(pz, texel(m, i + 1, j)) != s0;
-    int du = shadow_test(pz, texel(m, i, j + 1)) != s0;
-    int dd = shadow_test(pz, texel(m, i, j - 1)) != s0;
-    uint32_t d4 = dl | (dr << 1) | (du << 2) | (dd << 3);
+    float zl, zr, zu, zd;
+    if (i > 0 && i < m.width - 1 && j > 0 && j < m.height - 1) {
+        zl = __ldg(c - 1);
+        zr = __ldg(c + 1);
+        zu = __ldg(c + m.pitch);
+        zd = __ldg(c - m.pitch);
+    } else {
+        zl = texel(m, i - 1, j);
+        zr = texel(m, i + 1, j);
+        zu = texel(m, i, j + 1);
+        zd = texel(m, i, j - 1);
+    }
+    const uint32_t dl = shadow_test(pz, zl) != s0;
+    const uint32_t dr = shadow_test(pz, zr) != s0;
+    const uint32_t du = shadow_test(pz, zu) != s0;
+    const uint32_t dd = shadow_test(pz, zd) != s0;
+    const uint32_t d4 = dl | (dr << 1) | (du << 2) | (dd << 3);
     bits = (uint32_t)s0 | (d4 << 1);
     r.code = (uint16_t)(d4 | ((1 - s0) << 4));
-    float s = (float)s0;
-    r.sil = (MODE & 1) ? ((s0 == 0) ? 0.0f : s) : 0.0f;
+    const float s = (float)s0;
+    r.sil = s;
     r.fil = s;
-    bool edge = d4 != 0;
+    const bool edge = d4 != 0;
     if (MODE == 1)
         return edge && s0 == 1;
     return edge;
@@ -217,148 +273,183 @@ __device__ __forceinline__ void resolve_edge(const MapDev &m, float x, float y, 
         r.fil = filter(dx3, dy3, 1 - s0, ex, ey, nx, ny);
 }
 
-// Shared memory of one CTA for a tile of kThreads * kPerThread fragments.
-template <int kThreads>
-struct TileSmem {
-    static constexpr int kTile = kThreads * kPerThread;
-    float x[kTile];
-    float y[kTile];
-    float z[kTile];
-    float sil[kTile];
-    float fil[kTile];
-    uint16_t code[kTile];
-    uint32_t queue[kTile];      // slot | bits << 16
-    int queue_n;
+// ------------------------------------------------------------ warp tiles --
+//
+// A warp owns a tile of kWarpTile = 32 lanes x 4 consecutive fragments.  Warps
+// never wait for each other (no CTA barrier).  Per tile a warp classifies its
+// fragments, stores every answer at once (edge fragments get a provisional
+// value) and appends its edge fragments to its own shared-memory queue.  The
+// queue is drained 32 entries at a time, so the walks run with all 32 lanes
+// busy, and the drained answers overwrite the provisional ones (still in L2).
+// While a warp works on one tile, the loads of its next tile's coordinates
+// are already in flight (register double buffering).
+
+constexpr int kWarpTile = 32 * kPerThread;   // 128 fragments
+constexpr int kQueueCap = kWarpTile + 32;    // < 32 left over + one tile
+
+// One deferred edge fragment (24 bytes).
+struct EdgeEntry {
+    float x, y, z;
+    uint32_t bits_job;       // s0 | d4 << 1 (5 bits) | job << 8
+    long long idx;           // fragment index within the job
 };
 
-// Output pointers of one tile's fragments.
-struct TileIO {
+struct WarpQueue {
+    EdgeEntry q[kQueueCap];
+};
+
+// Coordinates of one warp tile held by a lane (4 fragments).
+struct LaneCoords {
+    float x[kPerThread], y[kPerThread], z[kPerThread];
+};
+
+// Where a warp tile lives: fragments [first, first + count) of a job.
+struct WarpTileIO {
     const float *x, *y, *z;
     float *sil, *fil;
     uint16_t *codes;
-    long long n;                // fragments in the job
-    long long first;            // first fragment of the tile
-    bool vec;                   // all planes 16-byte aligned
+    long long first;
+    int count;               // 1..kWarpTile
+    int job;
+    bool vec;                // count == kWarpTile and every plane 16-byte aligned
 };
+
+// Output side of a job, for the deferred answers.
+struct JobOut {
+    MapDev map;
+    float *sil, *fil;
+    uint16_t *codes;
+    int mode;
+};
+
+// Issue the loads of a warp tile.  Vector path: lane l owns fragments
+// 4l..4l+3 (one 16-byte load per plane).  Scalar path: lane l owns
+// fragments l, l+32, l+64, l+96 (coalesced 4-byte loads).
+__device__ __forceinline__ void load_tile(const WarpTileIO &t, unsigned lane, LaneCoords &c)
+{
+    if (t.vec) {
+        const float4 vx = __ldcs(reinterpret_cast<const float4 *>(t.x + t.first) + lane);
+        const float4 vy = __ldcs(reinterpret_cast<const float4 *>(t.y + t.first) + lane);
+        const float4 vz = __ldcs(reinterpret_cast<const float4 *>(t.z + t.first) + lane);
+        c.x[0] = vx.x; c.x[1] = vx.y; c.x[2] = vx.z; c.x[3] = vx.w;
+        c.y[0] = vy.x; c.y[1] = vy.y; c.y[2] = vy.z; c.y[3] = vy.w;
+        c.z[0] = vz.x; c.z[1] = vz.y; c.z[2] = vz.z; c.z[3] = vz.w;
+    } else {
+#pragma unroll
+        for (int e = 0; e < kPerThread; ++e) {
+            const int s = (int)lane + 32 * e;
+            const bool ok = s < t.count;
+            c.x[e] = ok ? __ldcs(t.x + t.first + s) : 0.0f;
+            c.y[e] = ok ? __ldcs(t.y + t.first + s) : 0.0f;
+            c.z[e] = ok ? __ldcs(t.z + t.first + s) : 0.0f;
+        }
+    }
+}
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
-// Append `want` to the CTA queue with one atomic per warp.
-__device__ __forceinline__ void queue_push(int &queue_n, uint32_t *queue, bool want, uint32_t entry)
+// Walk, normalise and answer one deferred edge fragment; write its answers.
+__device__ __forceinline__ void resolve_entry(const JobOut &o, const EdgeEntry &q, int max_dist)
 {
-    unsigned mask = __ballot_sync(0xffffffffu, want);
-    if (mask == 0)
-        return;
-    int leader = __ffs(mask) - 1;
-    int base = 0;
-    if ((int)lane_id() == leader)
-        base = atomicAdd(&queue_n, __popc(mask));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (want)
-        queue[base + __popc(mask & ((1u << lane_id()) - 1u))] = entry;
+    const uint32_t bits = q.bits_job & 0x1fu;
+    const uint32_t d4 = bits >> 1, s0 = bits & 1u;
+    FragResult r{0.0f, 0.0f, (uint16_t)(d4 | ((1u - s0) << 4))};
+    switch (o.mode) {
+    case 1: resolve_edge<1>(o.map, q.x, q.y, q.z, bits, max_dist, r); break;
+    case 2: resolve_edge<2>(o.map, q.x, q.y, q.z, bits, max_dist, r); break;
+    default: resolve_edge<3>(o.map, q.x, q.y, q.z, bits, max_dist, r); break;
+    }
+    if (o.mode & 1) o.sil[q.idx] = r.sil;
+    if (o.mode & 2) o.fil[q.idx] = r.fil;
+    if (o.codes) o.codes[q.idx] = r.code;
 }
 
-// Process one tile (all threads of the CTA call this; ends with a barrier).
-template <int MODE, bool CODES, int kThreads>
-__device__ __forceinline__ void process_tile(const MapDev &m, const TileIO &io, int max_dist,
-                                             TileSmem<kThreads> &sm)
+// Drain full rounds of 32 queued edge fragments (or everything when
+// `all`).  `jobs(job)` returns the JobOut of a job.  The count is uniform
+// across the warp.
+template <typename Jobs>
+__device__ __forceinline__ void drain_queue(const Jobs &jobs, WarpQueue &wq, int &count, int max_dist, bool all)
 {
-    constexpr int kTile = TileSmem<kThreads>::kTile;
-    const int t = threadIdx.x;
-    if (t == 0)
-        sm.queue_n = 0;
-    __syncthreads();
-
-    // --- 1. load.  Vector path: thread t owns slots 4t..4t+3.  Scalar path:
-    // thread t owns slots t, t + kThreads, ... (coalesced either way).
-    float xs[kPerThread], ys[kPerThread], zs[kPerThread];
-    int slot[kPerThread];
-    bool valid[kPerThread];
-    const long long remain = io.n - io.first;
-    if (io.vec && remain >= kTile) {
-        const float4 vx = __ldcs(reinterpret_cast<const float4 *>(io.x + io.first) + t);
-        const float4 vy = __ldcs(reinterpret_cast<const float4 *>(io.y + io.first) + t);
-        const float4 vz = __ldcs(reinterpret_cast<const float4 *>(io.z + io.first) + t);
-        xs[0] = vx.x; xs[1] = vx.y; xs[2] = vx.z; xs[3] = vx.w;
-        ys[0] = vy.x; ys[1] = vy.y; ys[2] = vy.z; ys[3] = vy.w;
-        zs[0] = vz.x; zs[1] = vz.y; zs[2] = vz.z; zs[3] = vz.w;
-#pragma unroll
-        for (int e = 0; e < kPerThread; ++e) {
-            slot[e] = kPerThread * t + e;
-            valid[e] = true;
+    const unsigned lane = lane_id();
+    while (count >= 32 || (all && count > 0)) {
+        __syncwarp();                      // queue entries and provisional stores are visible
+        const int base = count >= 32 ? count - 32 : 0;
+        const int k = base + (int)lane;
+        if (k < count) {
+            const EdgeEntry q = wq.q[k];
+            resolve_entry(jobs((int)(q.bits_job >> 8)), q, max_dist);
         }
-    } else {
-#pragma unroll
-        for (int e = 0; e < kPerThread; ++e) {
-            slot[e] = t + e * kThreads;
-            valid[e] = slot[e] < remain;
-            long long g = io.first + slot[e];
-            xs[e] = valid[e] ? __ldcs(io.x + g) : 0.0f;
-            ys[e] = valid[e] ? __ldcs(io.y + g) : 0.0f;
-            zs[e] = valid[e] ? __ldcs(io.z + g) : 0.0f;
-        }
+        __syncwarp();                      // entries read before they are overwritten
+        count = base;
     }
+}
 
-    // --- 2. classify; finish off-edge fragments, queue edge fragments.
+// Classify one warp tile whose coordinates the lane holds, store its answers
+// (provisional for edge fragments) and queue its edge fragments.
+template <int MODE, bool CODES>
+__device__ __forceinline__ void classify_warp_tile(const MapDev &m, const WarpTileIO &t, const LaneCoords &c,
+                                                   WarpQueue &wq, int &count)
+{
+    const unsigned lane = lane_id();
+    const unsigned below = (1u << lane) - 1u;
+    FragResult r[kPerThread];
 #pragma unroll
     for (int e = 0; e < kPerThread; ++e) {
-        FragResult r{0.0f, 0.0f, 0};
+        const int s = t.vec ? (int)(kPerThread * lane) + e : (int)lane + 32 * e;
+        r[e] = FragResult{0.0f, 0.0f, 0};
         uint32_t bits = 0;
         bool edge = false;
-        if (valid[e])
-            edge = classify<MODE, CODES>(m, xs[e], ys[e], zs[e], r, bits);
-        const int s = slot[e];
-        sm.x[s] = xs[e];
-        sm.y[s] = ys[e];
-        sm.z[s] = zs[e];
-        if (MODE & 1) sm.sil[s] = r.sil;
-        if (MODE & 2) sm.fil[s] = r.fil;
-        if (CODES) sm.code[s] = r.code;
-        queue_push(sm.queue_n, sm.queue, edge, (uint32_t)s | (bits << 16));
+        if (s < t.count)
+            edge = classify<MODE, CODES>(m, c.x[e], c.y[e], c.z[e], r[e], bits);
+        const unsigned mask = __ballot_sync(0xffffffffu, edge);
+        if (edge) {
+            EdgeEntry &q = wq.q[count + __popc(mask & below)];
+            q.x = c.x[e];
+            q.y = c.y[e];
+            q.z = c.z[e];
+            q.bits_job = bits | ((uint32_t)t.job << 8);
+            q.idx = t.first + s;
+        }
+        count += __popc(mask);
     }
-    __syncthreads();
-
-    // --- 3. drain the edge queue with converged lanes.
-    const int qn = sm.queue_n;
-    for (int q = t; q < qn; q += kThreads) {
-        const uint32_t entry = sm.queue[q];
-        const int s = entry & 0xffff;
-        const uint32_t bits = entry >> 16;
-        FragResult r;
-        r.code = CODES ? sm.code[s] : 0;
-        r.sil = 0.0f;
-        r.fil = 0.0f;
-        resolve_edge<MODE>(m, sm.x[s], sm.y[s], sm.z[s], bits, max_dist, r);
-        if (MODE & 1) sm.sil[s] = r.sil;
-        if (MODE & 2) sm.fil[s] = r.fil;
-        if (CODES) sm.code[s] = r.code;
-    }
-    __syncthreads();
-
-    // --- 4. store.
-    if (io.vec && remain >= kTile) {
+    if (t.vec) {
         if (MODE & 1)
-            __stcs(reinterpret_cast<float4 *>(io.sil + io.first) + t,
-                   reinterpret_cast<const float4 *>(sm.sil)[t]);
+            __stcg(reinterpret_cast<float4 *>(t.sil + t.first) + lane,
+                   make_float4(r[0].sil, r[1].sil, r[2].sil, r[3].sil));
         if (MODE & 2)
-            __stcs(reinterpret_cast<float4 *>(io.fil + io.first) + t,
-                   reinterpret_cast<const float4 *>(sm.fil)[t]);
+            __stcg(reinterpret_cast<float4 *>(t.fil + t.first) + lane,
+                   make_float4(r[0].fil, r[1].fil, r[2].fil, r[3].fil));
         if (CODES) {
-            const uint2 c = reinterpret_cast<const uint2 *>(sm.code)[t];
-            __stcs(reinterpret_cast<uint2 *>(io.codes + io.first) + t, c);
+            const uint2 cc = make_uint2((uint32_t)r[0].code | ((uint32_t)r[1].code << 16),
+                                        (uint32_t)r[2].code | ((uint32_t)r[3].code << 16));
+            __stcg(reinterpret_cast<uint2 *>(t.codes + t.first) + lane, cc);
         }
     } else {
 #pragma unroll
         for (int e = 0; e < kPerThread; ++e) {
-            if (!valid[e])
+            const int s = (int)lane + 32 * e;
+            if (s >= t.count)
                 continue;
-            const long long g = io.first + slot[e];
-            if (MODE & 1) io.sil[g] = sm.sil[slot[e]];
-            if (MODE & 2) io.fil[g] = sm.fil[slot[e]];
-            if (CODES) io.codes[g] = sm.code[slot[e]];
+            const long long g = t.first + s;
+            if (MODE & 1) t.sil[g] = r[e].sil;
+            if (MODE & 2) t.fil[g] = r[e].fil;
+            if (CODES) t.codes[g] = r[e].code;
         }
     }
-    __syncthreads();
+}
+
+// Dispatch on the runtime mode / codes pair of a job.
+__device__ __forceinline__ void classify_warp_tile_rt(int mode, bool codes, const MapDev &m, const WarpTileIO &t,
+                                                      const LaneCoords &c, WarpQueue &wq, int &count)
+{
+    switch (mode * 2 + (codes ? 1 : 0)) {
+    case 2: classify_warp_tile<1, false>(m, t, c, wq, count); break;
+    case 3: classify_warp_tile<1, true>(m, t, c, wq, count); break;
+    case 4: classify_warp_tile<2, false>(m, t, c, wq, count); break;
+    case 5: classify_warp_tile<2, true>(m, t, c, wq, count); break;
+    case 6: classify_warp_tile<3, false>(m, t, c, wq, count); break;
+    default: classify_warp_tile<3, true>(m, t, c, wq, count); break;
+    }
 }
 
 }  // namespace rbsm

@@ -74,20 +74,64 @@ MapDev to_dev(const rbsm_map &m) { return MapDev{m.depth, m.width, m.height, (lo
 
 // ---------------------------------------------------------------- kernel --
 
+// The single job of a plain launch, for the deferred edge answers.
+struct PlainJobs {
+    JobOut out;
+    __device__ __forceinline__ const JobOut &operator()(int) const { return out; }
+};
+
+// Persistent warps walk the warp tiles of one fragment set statically
+// (tile = global warp id + k * warps in the grid): consecutive warps hold
+// consecutive tiles, so the warps resident at one time gather from one
+// compact region of the shadow map.
 template <int MODE, bool CODES, int kThreads>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 1024 / kThreads)
 plain_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict__ y,
              const float *__restrict__ z, long long n, float *__restrict__ sil,
-             float *__restrict__ fil, uint16_t *__restrict__ codes, int max_dist, bool vec)
+             float *__restrict__ fil, uint16_t *__restrict__ codes, int max_dist, bool vec_planes)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto &sm = *reinterpret_cast<TileSmem<kThreads> *>(smem_raw);
-    constexpr long long kTile = TileSmem<kThreads>::kTile;
-    TileIO io{x, y, z, sil, fil, codes, n, 0, vec};
-    for (long long first = (long long)blockIdx.x * kTile; first < n; first += (long long)gridDim.x * kTile) {
-        io.first = first;
-        process_tile<MODE, CODES, kThreads>(m, io, max_dist, sm);
+    constexpr int kWarps = kThreads / 32;
+    __shared__ WarpQueue wq[kWarps];
+    const unsigned lane = lane_id();
+    const int warp = threadIdx.x >> 5;
+    const long long stride = (long long)gridDim.x * kWarps;
+    const long long tiles = (n + kWarpTile - 1) / kWarpTile;
+    long long tile = (long long)blockIdx.x * kWarps + warp;
+    if (tile >= tiles)
+        return;
+    const PlainJobs jobs{JobOut{m, sil, fil, CODES ? codes : nullptr, MODE}};
+    auto io_of = [&](long long tl) {
+        WarpTileIO t;
+        t.x = x; t.y = y; t.z = z; t.sil = sil; t.fil = fil; t.codes = codes;
+        t.first = tl * kWarpTile;
+        const long long left = n - t.first;
+        t.count = left < kWarpTile ? (int)left : kWarpTile;
+        t.job = 0;
+        t.vec = vec_planes && t.count == kWarpTile;
+        return t;
+    };
+    WarpTileIO t = io_of(tile);
+    LaneCoords c;
+    load_tile(t, lane, c);
+    int queued = 0;
+    for (;;) {
+        const long long nt = tile + stride;
+        const bool more = nt < tiles;
+        WarpTileIO tn;
+        LaneCoords cn;
+        if (more) {
+            tn = io_of(nt);
+            load_tile(tn, lane, cn);       // next tile's loads fly during this tile
+        }
+        classify_warp_tile<MODE, CODES>(m, t, c, wq[warp], queued);
+        drain_queue(jobs, wq[warp], queued, max_dist, false);
+        if (!more)
+            break;
+        tile = nt;
+        t = tn;
+        c = cn;
     }
+    drain_queue(jobs, wq[warp], queued, max_dist, true);
 }
 
 template <int MODE, bool CODES>
@@ -95,27 +139,26 @@ int launch_plain(const rbsm_map &map, const rbsm_frags &f, float *sil, float *fi
                  int max_dist, cudaStream_t stream)
 {
     constexpr int kThreads = 256;
-    constexpr long long kTile = TileSmem<kThreads>::kTile;
-    const size_t smem = sizeof(TileSmem<kThreads>);
     auto kern = plain_kernel<MODE, CODES, kThreads>;
     static KernelSetup setup;
     int occupancy = 0;
-    int rc = setup.get(kern, kThreads, smem, &occupancy);
+    int rc = setup.get(kern, kThreads, 0, &occupancy);
     if (rc != RBSM_OK)
         return rc;
     const int sms = device_sm_count();
     if (sms <= 0)
         return cuda_fail(cudaErrorNoDevice);
-    const long long tiles = (f.n + kTile - 1) / kTile;
+    const long long warp_tiles = (f.n + kWarpTile - 1) / kWarpTile;
+    const long long blocks_needed = (warp_tiles + kThreads / 32 - 1) / (kThreads / 32);
     long long grid = (long long)sms * occupancy;
-    if (grid > tiles)
-        grid = tiles;
+    if (grid > blocks_needed)
+        grid = blocks_needed;
     bool vec = aligned16(f.x) && aligned16(f.y) && aligned16(f.z);
     if (MODE & 1) vec = vec && aligned16(sil);
     if (MODE & 2) vec = vec && aligned16(fil);
     if (CODES) vec = vec && aligned16(codes);
-    kern<<<(unsigned)grid, kThreads, smem, stream>>>(to_dev(map), f.x, f.y, f.z, f.n, sil, fil, codes,
-                                                     max_dist, vec);
+    kern<<<(unsigned)grid, kThreads, 0, stream>>>(to_dev(map), f.x, f.y, f.z, f.n, sil, fil, codes,
+                                                  max_dist, vec);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return cuda_fail(e);

@@ -118,3 +118,29 @@ def test_bench_workload_through_the_batch(api):
             ref = orc.evaluate(fr.depth, fr.x, fr.y, fr.z, mode)
             codes = j.codes.cpu().numpy().view(np.uint16) if mode == orc.MODE_FILTER else None
             assert_parity(out.cpu().numpy(), codes, ref, mode, fr.name)
+
+
+def test_graph_replay_and_autotune(api, small_c3, tmp_path):
+    """The CUDA graph of a batch replays the same answers as direct launches;
+    the autotuner times the candidates, keeps answers correct, and its
+    choice is cached per batch signature."""
+    ref = _batch(api, small_c3, modes=[3], codes=True)
+    api.rbsm_batch_run(ref)
+    b = _batch(api, small_c3, modes=[3], codes=True)
+    g = api.BatchGraph(b)
+    for _ in range(3):
+        g.launch()
+    torch.cuda.synchronize()
+    for j, r in zip(b.jobs, ref.jobs):
+        assert torch.equal(j.vis_silhouette, r.vis_silhouette)
+        assert torch.equal(j.vis_filter, r.vis_filter)
+        assert torch.equal(j.codes, r.codes)
+    g.close()
+    cache = str(tmp_path / "tune.json")
+    t = api.rbsm_batch_autotune(b, repeats=2, cache=cache)
+    assert t["candidates"] == 8 and t["tile_threads"] in (128, 256, 512) and not t["cached"]
+    assert api.rbsm_batch_autotune(b, cache=cache)["cached"]
+    api.rbsm_batch_run(b)
+    torch.cuda.synchronize()
+    for j, r in zip(b.jobs, ref.jobs):
+        assert torch.equal(j.vis_filter, r.vis_filter)
