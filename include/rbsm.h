@@ -177,6 +177,33 @@ int rbsm_batch_workspace_size(const rbsm_batch *batch, size_t *bytes);
 int rbsm_batch_run(const rbsm_batch *batch, void *workspace, size_t workspace_bytes, void *stream);
 
 /*
+ * rbsm_batch_run without a workspace argument, for callers that cannot
+ * allocate device memory: a plugin running inside a host application that
+ * owns every device allocation, or a frame loop with a fixed memory budget
+ * that must not allocate while frames are in flight.  The paper has no
+ * counterpart; this is a convenience of the library.
+ *
+ * The scratch rbsm_batch_run keeps in the caller's workspace (work counter,
+ * status word, surrogate counters) lives instead in one device array
+ * compiled into the library, RBSM_NOALLOC_SCRATCH_BYTES bytes, which every
+ * GPU that loads the library holds until the process exits.  The call
+ * allocates nothing (no cudaMalloc, no cudaFree, no allocating library
+ * routine): it clears the counters with a stream-ordered memset and
+ * launches the same kernel as rbsm_batch_run, so its answers are the same.
+ *
+ * The first call on each device looks up the array's device address (with
+ * that device current), so make that first call before any stream capture
+ * on the calling thread.  Every call shares the one array and the array
+ * keeps the last call's contents: calls whose work overlaps on the GPU
+ * (other streams, other threads) race on it, so order them on one stream
+ * or use rbsm_batch_run with separate workspaces.  A batch whose workspace
+ * (rbsm_batch_workspace_size) exceeds the array is rejected with
+ * RBSM_ERR_WORKSPACE; other errors as for rbsm_batch_run.
+ */
+#define RBSM_NOALLOC_SCRATCH_BYTES 256
+int rbsm_batch_run_noalloc(const rbsm_batch *batch, void *stream);
+
+/*
  * CUDA graph of one batched launch (the workspace memset and the persistent
  * kernel), built once and replayed with one cudaGraphLaunch per frame.  The
  * graph captures the descriptors, the device pointers and the workspace as

@@ -7,6 +7,7 @@
 
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "rbsm.h"
 #include "rbsm_device.cuh"
@@ -643,3 +644,71 @@ int rbsm_batch_status(const void *workspace, int *status)
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------- allocation-free run --
+//
+// rbsm_batch_run_noalloc: the batched launch for callers that cannot
+// allocate device memory (see include/rbsm.h).  Its scratch, the same
+// work counter / status word / surrogate counters rbsm_batch_run keeps in a
+// caller-allocated workspace, lives in this file-scope device array instead.
+// Every GPU that loads the library holds the array until the process exits.
+// On the host, `g_noalloc_scratch` only names a host-side stand-in: the
+// kernel is given the device address cudaGetSymbolAddress reports, looked up
+// once per device (with that device current) on the first call there.
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RBSM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[rbsm::KernelSetup::kMaxDevices] = {};
+
+int noalloc_scratch_for_current_device(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return rbsm::cuda_fail(e);
+    if (dev < 0 || dev >= rbsm::KernelSetup::kMaxDevices)
+        return rbsm::cuda_fail(cudaErrorInvalidDevice);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess)
+            return rbsm::cuda_fail(e);
+        if (!p)
+            return rbsm::cuda_fail(cudaErrorInvalidSymbol);
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return RBSM_OK;
+}
+
+}  // namespace
+
+extern "C" int rbsm_batch_run_noalloc(const rbsm_batch *batch, void *stream)
+{
+    size_t need = 0;
+    int rc = rbsm_batch_workspace_size(batch, &need);
+    if (rc != RBSM_OK)
+        return rc;
+    if (need > (size_t)RBSM_NOALLOC_SCRATCH_BYTES)
+        return RBSM_ERR_WORKSPACE;           // this batch needs more scratch than the array holds
+    static thread_local rbsm::BatchArgs args;
+    int threads = 0;
+    if ((rc = rbsm::prepare_batch(batch, args, &threads)) != RBSM_OK)
+        return rc;
+    void *scratch = nullptr;
+    if ((rc = noalloc_scratch_for_current_device(&scratch)) != RBSM_OK)
+        return rc;
+    rbsm::bind_workspace(args, scratch);
+    if (args.total_tiles == 0)
+        return RBSM_OK;
+    rbsm::LaunchShape sh;
+    if ((rc = rbsm::launch_shape(args, threads, batch->ctas_per_sm, &sh)) != RBSM_OK)
+        return rc;
+    // enqueue_batch clears the counters that must start at zero (a memset of
+    // the array's first 32 bytes, stream-ordered before the kernel)
+    return rbsm::enqueue_batch(args, sh, scratch, reinterpret_cast<cudaStream_t>(stream));
+}
