@@ -197,8 +197,10 @@ struct FragResult {
 // Steps 1-2 for one fragment: texel, shadow test, four-neighbourhood.
 // Returns true when the fragment needs the edge walk for this mode; packs
 // s0 and the four directions into `bits` (bit 0 = s0, bits 1-4 = left,
-// right, +y, -y).  Away from the border the four neighbours are plain
-// offsets (+-1, +-pitch) of the centre texel's address.
+// right, +y, -y).  Clamp-to-edge is applied branch-free: a neighbour
+// outside the map is the centre texel itself, so the five loads of a
+// fragment (and of the other fragments of the lane) can all be in flight at
+// once.
 template <int MODE, bool CODES>
 __device__ __forceinline__ bool classify(const MapDev &m, float x, float y, float pz,
                                          FragResult &r, uint32_t &bits)
@@ -208,7 +210,8 @@ __device__ __forceinline__ bool classify(const MapDev &m, float x, float y, floa
     texel_coord(x, m.width, i, fx);
     texel_coord(y, m.height, j, fy);
     const float *c = m.depth + (long long)j * m.pitch + i;
-    const int s0 = shadow_test(pz, __ldg(c));
+    const float zc = __ldg(c);
+    const int s0 = shadow_test(pz, zc);
     // Listing 1: in silhouette recovery a shadowed fragment stays shadowed and
     // needs no neighbourhood (unless codes are requested).
     if (MODE == 1 && !CODES && s0 == 0) {
@@ -217,18 +220,14 @@ __device__ __forceinline__ bool classify(const MapDev &m, float x, float y, floa
         bits = 0;
         return false;
     }
-    float zl, zr, zu, zd;
-    if (i > 0 && i < m.width - 1 && j > 0 && j < m.height - 1) {
-        zl = __ldg(c - 1);
-        zr = __ldg(c + 1);
-        zu = __ldg(c + m.pitch);
-        zd = __ldg(c - m.pitch);
-    } else {
-        zl = texel(m, i - 1, j);
-        zr = texel(m, i + 1, j);
-        zu = texel(m, i, j + 1);
-        zd = texel(m, i, j - 1);
-    }
+    const long long up = j < m.height - 1 ? m.pitch : 0;
+    const long long dn = j > 0 ? m.pitch : 0;
+    const int lf = i > 0 ? 1 : 0;
+    const int rt = i < m.width - 1 ? 1 : 0;
+    const float zl = __ldg(c - lf);
+    const float zr = __ldg(c + rt);
+    const float zu = __ldg(c + up);
+    const float zd = __ldg(c - dn);
     const uint32_t dl = shadow_test(pz, zl) != s0;
     const uint32_t dr = shadow_test(pz, zr) != s0;
     const uint32_t du = shadow_test(pz, zu) != s0;
@@ -236,9 +235,9 @@ __device__ __forceinline__ bool classify(const MapDev &m, float x, float y, floa
     const uint32_t d4 = dl | (dr << 1) | (du << 2) | (dd << 3);
     bits = (uint32_t)s0 | (d4 << 1);
     r.code = (uint16_t)(d4 | ((1 - s0) << 4));
-    const float s = (float)s0;
-    r.sil = s;
-    r.fil = s;
+    const float sv = (float)s0;
+    r.sil = sv;
+    r.fil = sv;
     const bool edge = d4 != 0;
     if (MODE == 1)
         return edge && s0 == 1;
@@ -393,21 +392,35 @@ __device__ __forceinline__ void classify_warp_tile(const MapDev &m, const WarpTi
     const unsigned lane = lane_id();
     const unsigned below = (1u << lane) - 1u;
     FragResult r[kPerThread];
+    uint32_t bits[kPerThread];
+    bool edge[kPerThread];
+    // classify the lane's four fragments first (no warp-wide step in between,
+    // so all their texel loads are issued back to back) ...
+    if (t.vec) {
+#pragma unroll
+        for (int e = 0; e < kPerThread; ++e)
+            edge[e] = classify<MODE, CODES>(m, c.x[e], c.y[e], c.z[e], r[e], bits[e]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < kPerThread; ++e) {
+            r[e] = FragResult{0.0f, 0.0f, 0};
+            bits[e] = 0;
+            edge[e] = false;
+            if ((int)lane + 32 * e < t.count)
+                edge[e] = classify<MODE, CODES>(m, c.x[e], c.y[e], c.z[e], r[e], bits[e]);
+        }
+    }
+    // ... then queue the edge fragments, one ballot per element
 #pragma unroll
     for (int e = 0; e < kPerThread; ++e) {
         const int s = t.vec ? (int)(kPerThread * lane) + e : (int)lane + 32 * e;
-        r[e] = FragResult{0.0f, 0.0f, 0};
-        uint32_t bits = 0;
-        bool edge = false;
-        if (s < t.count)
-            edge = classify<MODE, CODES>(m, c.x[e], c.y[e], c.z[e], r[e], bits);
-        const unsigned mask = __ballot_sync(0xffffffffu, edge);
-        if (edge) {
+        const unsigned mask = __ballot_sync(0xffffffffu, edge[e]);
+        if (edge[e]) {
             EdgeEntry &q = wq.q[count + __popc(mask & below)];
             q.x = c.x[e];
             q.y = c.y[e];
             q.z = c.z[e];
-            q.bits_job = bits | ((uint32_t)t.job << 8);
+            q.bits_job = bits[e] | ((uint32_t)t.job << 8);
             q.idx = t.first + s;
         }
         count += __popc(mask);
