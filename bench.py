@@ -53,6 +53,8 @@ def parse_args(argv=None):
     p.add_argument("--skip-cpu", action="store_true", help="profiling runs only")
     p.add_argument("--skip-learned", action="store_true", help="profiling runs only")
     p.add_argument("--guard-tau", type=float, default=0.05, help="surrogate guard (largest accepted error estimate)")
+    p.add_argument("--texture", choices=["on", "off"], default="on",
+                   help="read each map's four-neighbourhood with texture gathers (rbsm_map_texture_create)")
     p.add_argument("--tile-threads", type=int, default=0)
     p.add_argument("--ctas-per-sm", type=int, default=0)
     return p.parse_args(argv)
@@ -282,7 +284,8 @@ def run_ours(args, rank, world, local_rank):
     maps = [h["depth"].to(device, non_blocking=True) for h in host]
     xyz = [h["xyz"].to(device, non_blocking=True) for h in host]
     jobs = [api.Job(k, xyz[k][0], xyz[k][1], xyz[k][2], mode=3) for k in range(frames)]
-    batch = api.Batch(maps, jobs, tile_threads=args.tile_threads, ctas_per_sm=args.ctas_per_sm)
+    texs = [api.MapTexture(m) for m in maps] if args.texture == "on" else None
+    batch = api.Batch(texs or maps, jobs, tile_threads=args.tile_threads, ctas_per_sm=args.ctas_per_sm)
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
 
@@ -353,7 +356,7 @@ def run_ours(args, rank, world, local_rank):
 
     learned = None
     if not args.skip_learned:
-        learned = compare_learned(api, maps, xyz, frames, n_frag, args, stream)
+        learned = compare_learned(api, texs or maps, xyz, frames, n_frag, args, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
@@ -370,7 +373,8 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "inputs larger than L2 (%.1f GB per step), no flush" % (
                        sum(h["depth"].numel() * 4 + h["xyz"].numel() * 4 for h in host) / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "tile_threads": args.tile_threads or 256, "ctas_per_sm": args.ctas_per_sm or "occupancy"},
+                   "tile_threads": args.tile_threads or 256, "ctas_per_sm": args.ctas_per_sm or "occupancy",
+                   "neighbourhood": "texture gathers" if texs else "plain loads"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
                      else "fallback 6800 GB/s",

@@ -71,7 +71,26 @@ typedef struct {
     int32_t width;
     int32_t height;
     int64_t pitch;                 /* floats between rows, >= width */
+    uint64_t texture;              /* optional, 0 = none: a texture of this map from
+                                    * rbsm_map_texture_create; when given, the four-
+                                    * neighbourhood is read with two texture gathers */
 } rbsm_map;
+
+/*
+ * Texture view of a shadow map for faster neighbourhood reads: a
+ * cudaTextureObject_t over the map's own memory (no copy) with point
+ * sampling, clamp-to-edge addressing and unnormalised coordinates, so two
+ * 2x2 texture gathers return the fragment's texel and its four neighbours
+ * (Listing 2) with the clamp of R2 done by the texture unit.  Answers are
+ * identical with and without it.  Creation is a set-up call (it creates a
+ * driver object, no device memory); destroy the texture with
+ * rbsm_map_texture_destroy once every launch that reads it has completed.
+ * Errors: RBSM_ERR_ARG for an invalid map, or for a base address or pitch
+ * that the device's texture alignment rules reject (use the map without a
+ * texture then); RBSM_ERR_CUDA when the driver refuses.
+ */
+int rbsm_map_texture_create(const rbsm_map *map, uint64_t *texture);
+int rbsm_map_texture_destroy(uint64_t texture);
 
 /* A set of light-space fragments (device memory, owned by the caller). */
 typedef struct {

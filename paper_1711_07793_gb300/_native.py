@@ -28,7 +28,7 @@ RBSM_BATCH_MAX_JOBS = 256
 
 class rbsm_map(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_void_p), ("width", ctypes.c_int32),
-                ("height", ctypes.c_int32), ("pitch", ctypes.c_int64)]
+                ("height", ctypes.c_int32), ("pitch", ctypes.c_int64), ("texture", ctypes.c_uint64)]
 
 
 class rbsm_frags(ctypes.Structure):
@@ -87,6 +87,10 @@ def _declare(lib):
         f = getattr(lib, name)
         f.restype = i32
         f.argtypes = [_P(rbsm_map), _P(rbsm_frags), vp, vp, _P(rbsm_params), vp]
+    lib.rbsm_map_texture_create.restype = i32
+    lib.rbsm_map_texture_create.argtypes = [_P(rbsm_map), _P(ctypes.c_uint64)]
+    lib.rbsm_map_texture_destroy.restype = i32
+    lib.rbsm_map_texture_destroy.argtypes = [ctypes.c_uint64]
     lib.rbsm_batch_workspace_size.restype = i32
     lib.rbsm_batch_workspace_size.argtypes = [_P(rbsm_batch), _P(ctypes.c_size_t)]
     lib.rbsm_batch_run.restype = i32

@@ -32,15 +32,50 @@ def _check_plane(name, t, n=None):
         raise ValueError("%s has %d elements, expected %d" % (name, t.shape[0], n))
 
 
-def map_desc(depth):
-    """rbsm_map for a (height, width) float32 CUDA tensor with unit inner stride."""
+class MapTexture:
+    """Texture view of a shadow map (rbsm_map_texture_create): the map's
+    four-neighbourhood is then read with two texture gathers.  Keep the
+    depth tensor alive while the texture is used; close() (or garbage
+    collection) destroys the texture, so do that only after the launches
+    that read it have completed."""
+
+    def __init__(self, depth):
+        self.depth = depth
+        m = _plain_map_desc(depth)
+        h = ctypes.c_uint64(0)
+        N.check("rbsm_map_texture_create", N.lib().rbsm_map_texture_create(ctypes.byref(m), ctypes.byref(h)))
+        self.handle = h.value
+
+    def close(self):
+        if self.handle:
+            N.check("rbsm_map_texture_destroy", N.lib().rbsm_map_texture_destroy(self.handle))
+        self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _plain_map_desc(depth):
     if not isinstance(depth, torch.Tensor) or depth.dtype != torch.float32 or depth.dim() != 2:
         raise TypeError("depth must be a 2-D float32 tensor")
     if not depth.is_cuda:
         raise TypeError("depth must be a CUDA tensor")
     if depth.stride(1) != 1 or depth.stride(0) < depth.shape[1]:
         raise ValueError("depth rows must be contiguous (pitch >= width)")
-    return N.rbsm_map(depth.data_ptr(), depth.shape[1], depth.shape[0], depth.stride(0))
+    return N.rbsm_map(depth.data_ptr(), depth.shape[1], depth.shape[0], depth.stride(0), 0)
+
+
+def map_desc(depth):
+    """rbsm_map for a (height, width) float32 CUDA tensor with unit inner
+    stride, or for a MapTexture (its map with the texture attached)."""
+    if isinstance(depth, MapTexture):
+        m = _plain_map_desc(depth.depth)
+        m.texture = depth.handle
+        return m
+    return _plain_map_desc(depth)
 
 
 def frags_desc(x, y, z):
@@ -71,7 +106,7 @@ def _host_roundtrip(fn, depth, x, y, z, codes, max_dist):
 
 
 def _single(cfn, fname, depth, x, y, z, vis=None, codes=False, max_dist=N.RBSM_MAXDIST_DEFAULT, stream=None):
-    if not depth.is_cuda:
+    if not isinstance(depth, MapTexture) and not depth.is_cuda:
         return _host_roundtrip(lambda *a, **k: _single(cfn, fname, *a, **k), depth, x, y, z, codes, max_dist)
     m = map_desc(depth)
     f = frags_desc(x, y, z)
@@ -202,7 +237,7 @@ class BatchGraph:
 def batch_signature(batch):
     """Key of a batch for the autotuner cache: device, map sizes, job sizes."""
     name = torch.cuda.get_device_name(batch.jobs[0].x.device)
-    maps = [tuple(m.shape) for m in batch.maps]
+    maps = [tuple(m.depth.shape) + ("tex",) if isinstance(m, MapTexture) else tuple(m.shape) for m in batch.maps]
     jobs = [(j.map_index, j.mode, int(j.x.shape[0]), j.codes is not None) for j in batch.jobs]
     return json.dumps([name, maps, jobs])
 

@@ -24,6 +24,7 @@ struct MapDev {
     int32_t width;
     int32_t height;
     long long pitch;
+    cudaTextureObject_t tex;     // 0 = none (plain loads)
 };
 
 // Nearest texel with clamp-to-edge addressing; read through the read-only
@@ -194,6 +195,34 @@ struct FragResult {
     uint16_t code;
 };
 
+// Steps 1-2 from the five depths of the texel and its neighbours.
+template <int MODE, bool CODES>
+__device__ __forceinline__ bool classify_from(float pz, float zc, float zl, float zr, float zu, float zd,
+                                              FragResult &r, uint32_t &bits)
+{
+    const int s0 = shadow_test(pz, zc);
+    if (MODE == 1 && !CODES && s0 == 0) {
+        r.sil = 0.0f;
+        r.code = 0;
+        bits = 0;
+        return false;
+    }
+    const uint32_t dl = shadow_test(pz, zl) != s0;
+    const uint32_t dr = shadow_test(pz, zr) != s0;
+    const uint32_t du = shadow_test(pz, zu) != s0;
+    const uint32_t dd = shadow_test(pz, zd) != s0;
+    const uint32_t d4 = dl | (dr << 1) | (du << 2) | (dd << 3);
+    bits = (uint32_t)s0 | (d4 << 1);
+    r.code = (uint16_t)(d4 | ((1 - s0) << 4));
+    const float sv = (float)s0;
+    r.sil = sv;
+    r.fil = sv;
+    const bool edge = d4 != 0;
+    if (MODE == 1)
+        return edge && s0 == 1;
+    return edge;
+}
+
 // Steps 1-2 for one fragment: texel, shadow test, four-neighbourhood.
 // Returns true when the fragment needs the edge walk for this mode; packs
 // s0 and the four directions into `bits` (bit 0 = s0, bits 1-4 = left,
@@ -209,6 +238,15 @@ __device__ __forceinline__ bool classify(const MapDev &m, float x, float y, floa
     float fx, fy;
     texel_coord(x, m.width, i, fx);
     texel_coord(y, m.height, j, fy);
+    if (m.tex) {
+        // two 2x2 gathers (point sampling, clamp to edge, unnormalised
+        // coordinates): at (i, j) the footprint is columns i-1..i, rows
+        // j-1..j; at (i+1, j+1) it is columns i..i+1, rows j..j+1.  Gather
+        // order: x = (lo col, hi row), y = (hi, hi), z = (hi, lo), w = (lo, lo).
+        const float4 a = tex2Dgather<float4>(m.tex, (float)i, (float)j, 0);
+        const float4 b = tex2Dgather<float4>(m.tex, (float)(i + 1), (float)(j + 1), 0);
+        return classify_from<MODE, CODES>(pz, a.y, a.x, b.z, b.x, a.z, r, bits);
+    }
     const float *c = m.depth + (long long)j * m.pitch + i;
     const float zc = __ldg(c);
     const int s0 = shadow_test(pz, zc);

@@ -70,7 +70,10 @@ int device_sm_count()
     return sms;
 }
 
-MapDev to_dev(const rbsm_map &m) { return MapDev{m.depth, m.width, m.height, (long long)m.pitch}; }
+MapDev to_dev(const rbsm_map &m)
+{
+    return MapDev{m.depth, m.width, m.height, (long long)m.pitch, (cudaTextureObject_t)m.texture};
+}
 
 // ---------------------------------------------------------------- kernel --
 
@@ -215,6 +218,59 @@ const char *rbsm_status_string(int code)
 }
 
 int rbsm_last_cuda_error(void) { return rbsm::g_last_cuda_error; }
+
+int rbsm_map_texture_create(const rbsm_map *map, uint64_t *texture)
+{
+    if (!texture)
+        return RBSM_ERR_ARG;
+    *texture = 0;
+    int rc = rbsm::check_map(map);
+    if (rc != RBSM_OK)
+        return rc;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return rbsm::cuda_fail(e);
+    int align = 0, pitch_align = 0, max_w = 0, max_h = 0, max_pitch = 0;
+    if ((e = cudaDeviceGetAttribute(&align, cudaDevAttrTextureAlignment, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&pitch_align, cudaDevAttrTexturePitchAlignment, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&max_w, cudaDevAttrMaxTexture2DLinearWidth, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&max_h, cudaDevAttrMaxTexture2DLinearHeight, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&max_pitch, cudaDevAttrMaxTexture2DLinearPitch, dev)) != cudaSuccess)
+        return rbsm::cuda_fail(e);
+    const long long pitch_bytes = map->pitch * 4;
+    if (align <= 0 || pitch_align <= 0 || (reinterpret_cast<uintptr_t>(map->depth) % (uintptr_t)align) != 0 ||
+        pitch_bytes % pitch_align != 0 || map->width > max_w || map->height > max_h || pitch_bytes > max_pitch)
+        return RBSM_ERR_ARG;
+    cudaResourceDesc res;
+    std::memset(&res, 0, sizeof(res));
+    res.resType = cudaResourceTypePitch2D;
+    res.res.pitch2D.devPtr = const_cast<float *>(map->depth);
+    res.res.pitch2D.desc = cudaCreateChannelDesc<float>();
+    res.res.pitch2D.width = (size_t)map->width;
+    res.res.pitch2D.height = (size_t)map->height;
+    res.res.pitch2D.pitchInBytes = (size_t)pitch_bytes;
+    cudaTextureDesc td;
+    std::memset(&td, 0, sizeof(td));
+    td.addressMode[0] = cudaAddressModeClamp;
+    td.addressMode[1] = cudaAddressModeClamp;
+    td.filterMode = cudaFilterModePoint;
+    td.readMode = cudaReadModeElementType;
+    td.normalizedCoords = 0;
+    cudaTextureObject_t tex = 0;
+    if ((e = cudaCreateTextureObject(&tex, &res, &td, nullptr)) != cudaSuccess)
+        return rbsm::cuda_fail(e);
+    *texture = (uint64_t)tex;
+    return RBSM_OK;
+}
+
+int rbsm_map_texture_destroy(uint64_t texture)
+{
+    if (texture == 0)
+        return RBSM_OK;
+    cudaError_t e = cudaDestroyTextureObject((cudaTextureObject_t)texture);
+    return e == cudaSuccess ? RBSM_OK : rbsm::cuda_fail(e);
+}
 
 int rbsm_version(void) { return 100; }
 

@@ -144,3 +144,25 @@ def test_graph_replay_and_autotune(api, small_c3, tmp_path):
     torch.cuda.synchronize()
     for j, r in zip(b.jobs, ref.jobs):
         assert torch.equal(j.vis_filter, r.vis_filter)
+
+
+def test_batch_with_textures_matches_plain_loads(api, small_c3):
+    """Maps given with textures (two gathers per fragment) give the same
+    answers as the same batch with plain loads, in every mode."""
+    ref = _batch(api, small_c3, modes=[3, 1, 2])
+    api.rbsm_batch_run(ref)
+    maps = [dev(m) for m in small_c3.maps]
+    texs = [api.MapTexture(m) for m in maps]
+    jobs = [api.Job(j.map_index, dev(j.x), dev(j.y), dev(j.z), mode=[3, 1, 2][k % 3], codes=True)
+            for k, j in enumerate(small_c3.jobs)]
+    b = api.Batch(texs, jobs)
+    api.rbsm_batch_run(b)
+    torch.cuda.synchronize()
+    for j, r in zip(b.jobs, ref.jobs):
+        if j.mode & 1:
+            assert torch.equal(j.vis_silhouette, r.vis_silhouette)
+        if j.mode & 2:
+            assert torch.equal(j.vis_filter, r.vis_filter)
+        assert torch.equal(j.codes, r.codes)
+    for t in texs:
+        t.close()

@@ -33,7 +33,7 @@ def dev(a):
 
 
 def run_gpu(api, depth, x, y, z, mode, max_dist=16, codes=True):
-    d = depth if isinstance(depth, torch.Tensor) else dev(depth)
+    d = depth if isinstance(depth, (torch.Tensor, api.MapTexture)) else dev(depth)
     fn = api.rbsm_visibility if mode == orc.MODE_SILHOUETTE else api.rsmss_filter
     xs, ys, zs = (t if isinstance(t, torch.Tensor) else dev(t) for t in (x, y, z))
     vis, cod = fn(d, xs, ys, zs, codes=codes, max_dist=max_dist)
@@ -194,3 +194,41 @@ def test_host_buffers_roundtrip(api):
     vis_h, cod_h = api.rsmss_filter(*args, codes=True)
     ref = orc.evaluate(f.depth, f.x, f.y, f.z, orc.MODE_FILTER)
     assert_parity(vis_h.numpy(), cod_h.numpy().view(np.uint16), ref, orc.MODE_FILTER, "host")
+
+
+def _try_texture(api, depth):
+    from paper_1711_07793_gb300 import _native as N
+    try:
+        return api.MapTexture(depth)
+    except N.RBSMError as e:
+        assert e.code == N.RBSM_ERR_ARG
+        return None
+
+
+@pytest.mark.parametrize("which", ["C1", "C2", "odd"])
+def test_texture_gather_path(api, which):
+    """The texture-gather neighbourhood (rbsm_map_texture_create) gives
+    exactly the same codes and answers as the plain loads, clamp-to-edge
+    included (maps down to 1 x 1)."""
+    import rbsm_scenes as sc
+    cases = []
+    if which == "C1":
+        f = sc.config1(4)
+        cases.append((f.depth, f.x, f.y, f.z))
+    elif which == "C2":
+        f = sc.config2(1, screen=(960, 540))
+        cases.append((f.depth, f.x, f.y, f.z))
+    else:
+        rng = np.random.default_rng(77)
+        for w, h in [(1, 1), (2, 2), (1, 9), (9, 1), (64, 48), (257, 129)]:
+            cases.append(_random_case(rng, w, h, 20000, spread=0.2))
+    for depth, x, y, z in cases:
+        d = dev(depth)
+        tex = _try_texture(api, d)
+        if tex is None:
+            continue
+        for mode in (orc.MODE_SILHOUETTE, orc.MODE_FILTER):
+            ref = orc.evaluate(depth, x, y, z, mode)
+            vis, cod = run_gpu(api, tex, x, y, z, mode)
+            assert_parity(vis, cod, ref, mode, "texture %s %s mode %d" % (which, depth.shape, mode))
+        tex.close()
