@@ -64,6 +64,7 @@ extern "C" {
 #define RBSM_MAXDIST_DEFAULT 16    /* §3.1.3: the value the paper used */
 #define RBSM_MAXDIST_LIMIT 255
 #define RBSM_MAX_EXTENT 65536      /* width and height limit of a shadow map */
+#define RBSM_MAX_FRAGMENTS 2147483647LL   /* fragments per fragment set (rbsm_frags.n) */
 
 /* A shadow map (device memory, owned by the caller). */
 typedef struct {
@@ -97,7 +98,7 @@ typedef struct {
     const float *x;
     const float *y;
     const float *z;
-    int64_t n;                     /* >= 0; n == 0 enqueues nothing */
+    int64_t n;                     /* 0..RBSM_MAX_FRAGMENTS; n == 0 enqueues nothing */
 } rbsm_frags;
 
 typedef struct {
@@ -117,7 +118,8 @@ typedef struct {
  *   vis:   output, n floats, each 0.0 or 1.0.
  *   codes: optional output, n uint16 (see above); NULL to skip.
  * Errors: RBSM_ERR_ARG for NULL map/frags/vis, NULL planes with n > 0,
- * width or height outside 1..RBSM_MAX_EXTENT, pitch < width, n < 0,
+ * width or height outside 1..RBSM_MAX_EXTENT, pitch < width, n outside
+ * 0..RBSM_MAX_FRAGMENTS,
  * max_dist outside 1..RBSM_MAXDIST_LIMIT, flags != 0; RBSM_ERR_CUDA when the
  * launch fails.
  */
@@ -163,8 +165,8 @@ typedef struct {
     rbsm_params params;
     int32_t tile_threads;          /* CTA size: 128, 256 or 512 threads; 0 = default 256 */
     int32_t ctas_per_sm;           /* persistent CTAs per SM, 1..8; 0 = occupancy limit.  At
-                                    * 256 threads, 5 or 6 select a variant compiled for 5 or
-                                    * 6 CTAs per SM (fewer registers per thread) */
+                                    * 256 threads, 3 selects a variant compiled for 3 CTAs per
+                                    * SM (more registers per thread) */
     /* Learned penumbra (not in the paper): NULL = exact everywhere.  Given a
      * network state block (rbsm_mlp_state_bytes), FILTER-mode jobs answer
      * their edge fragments with the surrogate wherever its own error
@@ -239,9 +241,9 @@ int rbsm_batch_graph_launch(rbsm_graph graph, void *stream);
 int rbsm_batch_graph_destroy(rbsm_graph graph);
 
 /*
- * Autotuner of the batched launch shape.  Times 8 candidate (CTA size,
+ * Autotuner of the batched launch shape.  Times 6 candidate (CTA size,
  * CTAs per SM) pairs: 128 threads at its occupancy limit; 256 threads at 2,
- * 3, 4 (occupancy limit), 5 and 6 CTAs per SM; 512 threads at 1 and 2.
+ * 3 and 4 (occupancy limit) CTAs per SM; 512 threads at 1 and 2.
  * Every warp works on its own 128-fragment tiles whatever the CTA size.
  * Each candidate gets `repeats` launches
  * each after one warm-up, on `stream`, and returns the fastest in *best.

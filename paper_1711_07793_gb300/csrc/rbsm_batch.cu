@@ -1,5 +1,5 @@
 // Batched evaluation: many shadow maps x many fragment sets in one
-// persistent launch.  CTAs take (job, tile) work items from an atomic
+// persistent launch (host side; the kernel is in rbsm_batch_kernel.cuh).  CTAs take (job, tile) work items from an atomic
 // counter in the caller's workspace, so maps of very different sizes and
 // views of very different resolutions share the GPU without a launch per
 // pair and without idle SMs at the end of small jobs.
@@ -11,276 +11,83 @@
 
 #include "rbsm.h"
 #include "rbsm_device.cuh"
+#include "rbsm_batch_kernel.cuh"
 #include "rbsm_host.h"
 #include "rbsm_mlp.cuh"
 
 namespace rbsm {
 
-struct BatchJobDev {
-    const float *x, *y, *z;
-    float *sil, *fil;
-    uint16_t *codes;
-    long long n;
-    long long tile_start;        // first work item of the job
-    int map;
-    int mode;                    // 1, 2, 3
-    int vec;                     // all planes 16-byte aligned
-    int codes_on;
-};
-
-// Passed by value as a __grid_constant__ kernel parameter (about 21 KB,
-// inside the 32 KB parameter space), so no descriptor copy to the device
-// is needed and the launch can be captured into a CUDA graph as is.
-struct BatchArgs {
-    MapDev maps[RBSM_BATCH_MAX_MAPS];
-    BatchJobDev jobs[RBSM_BATCH_MAX_JOBS];
-    int n_jobs;
-    int max_dist;
-    long long total_tiles;
-    unsigned long long *counter;
-    int *status;
-    const void *mlp;                 // surrogate state block or nullptr
-    float tau;                       // guard: largest accepted error estimate
-    unsigned long long *stats;       // [0] surrogate answers, [1] fallbacks
-};
-
-constexpr size_t kWorkspaceBytes = 256;
-constexpr int kChunkTiles = 8;       // warp tiles per claim of the work counter
-
-__device__ __forceinline__ int find_job(const BatchArgs &a, long long tile)
-{
-    int lo = 0, hi = a.n_jobs - 1;    // last job whose first tile <= tile
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (a.jobs[mid].tile_start <= tile)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ WarpTileIO job_tile(const BatchJobDev &J, int job, long long tile)
-{
-    WarpTileIO t;
-    t.x = J.x; t.y = J.y; t.z = J.z; t.sil = J.sil; t.fil = J.fil; t.codes = J.codes;
-    t.first = (tile - J.tile_start) * kWarpTile;
-    const long long left = J.n - t.first;
-    t.count = left < kWarpTile ? (int)left : kWarpTile;
-    t.job = job;
-    t.vec = J.vec && t.count == kWarpTile;
-    return t;
-}
-
-// Job table of a batched launch, for the deferred edge answers.
-struct BatchJobs {
-    const BatchArgs *a;
-    __device__ __forceinline__ JobOut operator()(int j) const
-    {
-        const BatchJobDev &J = a->jobs[j];
-        return JobOut{a->maps[J.map], J.sil, J.fil, J.codes_on ? J.codes : nullptr, J.mode};
-    }
-};
-
-// Shared memory of the learned variant: the network's weights and, per
-// warp, the 32 input rows and 32 outputs of one round of edge fragments.
-template <int kThreads>
-struct LearnedSmem {
-    mlp::SmemWeights w;
-    uint16_t feat[kThreads / 32][32 * mlp::kIn];
-    float out[kThreads / 32][32 * mlp::kOut];
-};
-
-// Drain rounds of up to 32 queued edge fragments with the surrogate: each
-// lane gathers its fragment's 5x5 features into one input row, the warp runs
-// the network on the 32 rows (two m16 tiles on the tensor cores), and each
-// fragment whose error estimate is within the guard takes the estimate,
-// clamped to [0, 1]; the others (and every fragment of a job that is not in
-// FILTER mode) take the exact walk.
-template <typename Jobs, int kThreads>
-__device__ __forceinline__ void drain_queue_learned(const Jobs &jobs, WarpQueue &wq, int &count, int max_dist,
-                                                    bool all, LearnedSmem<kThreads> &ls, int warp, float tau,
-                                                    unsigned long long *stats)
-{
-    const unsigned lane = lane_id();
-    const int g = lane >> 2, t = lane & 3;
-    uint16_t *feat = ls.feat[warp];
-    float *yout = ls.out[warp];
-    while (count >= 32 || (all && count > 0)) {
-        __syncwarp();
-        const int base = count >= 32 ? count - 32 : 0;
-        const int k = base + (int)lane;
-        const bool valid = k < count;
-        EdgeEntry q{0.0f, 0.0f, 0.0f, 0u, 0};
-        JobOut o{};
-        if (valid) {
-            q = wq.q[k];
-            o = jobs((int)(q.bits_job >> 8));
-        }
-        const bool use_net = valid && o.mode == 2;
-        if (use_net) {
-            uint32_t bits;
-            float fx, fy, gap;
-            fragment_features(o.map, q.x, q.y, q.z, bits, fx, fy, gap);
-            mlp::write_input_row(feat + lane * mlp::kIn, bits, fx, fy, gap);
-        } else {
-            uint4 *row = reinterpret_cast<uint4 *>(feat + lane * mlp::kIn);
-#pragma unroll
-            for (int w4 = 0; w4 < mlp::kIn / 8; ++w4)
-                row[w4] = make_uint4(0u, 0u, 0u, 0u);
-        }
-        __syncwarp();
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            uint32_t xa[2][4];
-            mlp::load_a(feat, mlp::kIn, mt * 16, 0, lane, xa[0]);
-            mlp::load_a(feat, mlp::kIn, mt * 16, 1, lane, xa[1]);
-            mlp::HiddenFrags h1, h2;
-            uint32_t m1, m2;
-            mlp::layer(xa, 2, ls.w.w1t, mlp::kIn, ls.w.b1, lane, h1, m1);
-            mlp::layer(h1.a, 4, ls.w.w2t, mlp::kHid, ls.w.b2, lane, h2, m2);
-            float y[4];
-            mlp::output_layer(h2, ls.w, lane, y);
-            if (t == 0) {
-                yout[(mt * 16 + g) * 2] = y[0];
-                yout[(mt * 16 + g) * 2 + 1] = y[1];
-                yout[(mt * 16 + g + 8) * 2] = y[2];
-                yout[(mt * 16 + g + 8) * 2 + 1] = y[3];
-            }
-        }
-        __syncwarp();
-        bool accepted = false;
-        if (use_net) {
-            const float v = yout[lane * 2], e = yout[lane * 2 + 1];
-            accepted = e <= tau && v == v;          // a NaN estimate never passes
-            if (accepted) {
-                const float vc = v < 0.0f ? 0.0f : (v > 1.0f ? 1.0f : v);
-                o.fil[q.idx] = vc;
-                if (o.codes) {
-                    const uint32_t bits = q.bits_job & 0x1fu;
-                    o.codes[q.idx] = (uint16_t)((bits >> 1) | ((1u - (bits & 1u)) << 4) | (1u << 10));
-                }
-            }
-        }
-        if (valid && !accepted)
-            resolve_entry(o, q, max_dist);
-        const unsigned acc_mask = __ballot_sync(0xffffffffu, accepted);
-        const unsigned fb_mask = __ballot_sync(0xffffffffu, use_net && !accepted);
-        if (lane == 0 && (acc_mask | fb_mask)) {
-            atomicAdd(&stats[0], (unsigned long long)__popc(acc_mask));
-            atomicAdd(&stats[1], (unsigned long long)__popc(fb_mask));
-        }
-        __syncwarp();
-        count = base;
-    }
-}
-
-// Persistent warps claim chunks of kChunkTiles warp tiles from the work
-// counter (one atomic per 1024 fragments).  The claim of the next chunk is
-// issued when the current one starts, and its value is read only when the
-// warp gets there, so the atomic's latency hides behind eight tiles of work.
-// Consecutive claims are consecutive tiles of the job list, so warps working
-// at the same time share the L2 footprint of one region of one map.
-// kMinBlocks: CTAs per SM the register allocation is sized for (64
-// registers per thread at 1024 threads per SM, 48 at 1280, 40 at 1536).
-template <int kThreads, bool LEARNED, int kMinBlocks>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const __grid_constant__ BatchArgs a)
-{
-    constexpr int kWarps = kThreads / 32;
-    __shared__ WarpQueue wq[kWarps];
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto &ls = *reinterpret_cast<LearnedSmem<kThreads> *>(smem_raw);
-    const unsigned lane = lane_id();
-    const int warp = threadIdx.x >> 5;
-    if (LEARNED) {
-        const mlp::State st = mlp::state_of(const_cast<void *>(a.mlp));
-        for (int k = threadIdx.x; k < mlp::kW1tElems; k += kThreads) ls.w.w1t[k] = st.w1t[k];
-        for (int k = threadIdx.x; k < mlp::kW2tElems; k += kThreads) ls.w.w2t[k] = st.w2t[k];
-        for (int k = threadIdx.x; k < mlp::kW3tElems; k += kThreads) ls.w.w3t[k] = st.w3t[k];
-        for (int k = threadIdx.x; k < mlp::kHid; k += kThreads) {
-            ls.w.b1[k] = st.master[mlp::kOffB1 + k];
-            ls.w.b2[k] = st.master[mlp::kOffB2 + k];
-        }
-        for (int k = threadIdx.x; k < mlp::kOutPad; k += kThreads)
-            ls.w.b3[k] = k < mlp::kOut ? st.master[mlp::kOffB3 + k] : 0.0f;
-        __syncthreads();
-    }
-    const long long total = a.total_tiles;
-    unsigned long long claim = 0;
-    if (lane == 0)
-        claim = atomicAdd(a.counter, 1ull);
-    long long tile = (long long)__shfl_sync(0xffffffffu, claim, 0) * kChunkTiles;
-    if (tile >= total)
-        return;
-    if (lane == 0)
-        claim = atomicAdd(a.counter, 1ull);      // next chunk, read later
-    int in_chunk = 0;
-    int job = find_job(a, tile);
-    WarpTileIO t = job_tile(a.jobs[job], job, tile);
-    LaneCoords c;
-    load_tile(t, lane, c);
-    const BatchJobs jobs{&a};
-    int queued = 0;
-    for (;;) {
-        long long nt;
-        if (in_chunk + 1 < kChunkTiles) {
-            nt = tile + 1;
-            in_chunk += 1;
-        } else {
-            nt = (long long)__shfl_sync(0xffffffffu, claim, 0) * kChunkTiles;
-            in_chunk = 0;
-            if (nt < total && lane == 0)
-                claim = atomicAdd(a.counter, 1ull);
-        }
-        const bool more = nt < total;
-        int njob = job;
-        WarpTileIO tn;
-        LaneCoords cn;
-        if (more) {
-            njob = find_job(a, nt);
-            tn = job_tile(a.jobs[njob], njob, nt);
-            load_tile(tn, lane, cn);           // next tile's loads fly during this tile
-        }
-        const BatchJobDev &J = a.jobs[job];
-        classify_warp_tile_rt(J.mode, J.codes_on != 0, a.maps[J.map], t, c, wq[warp], queued);
-        if (LEARNED)
-            drain_queue_learned<BatchJobs, kThreads>(jobs, wq[warp], queued, a.max_dist, false, ls, warp, a.tau,
-                                                     a.stats);
-        else
-            drain_queue(jobs, wq[warp], queued, a.max_dist, false);
-        if (!more)
-            break;
-        tile = nt;
-        job = njob;
-        t = tn;
-        c = cn;
-    }
-    if (LEARNED)
-        drain_queue_learned<BatchJobs, kThreads>(jobs, wq[warp], queued, a.max_dist, true, ls, warp, a.tau, a.stats);
-    else
-        drain_queue(jobs, wq[warp], queued, a.max_dist, true);
-}
-
-// Launch shape of a batched launch: grid and dynamic shared memory.  Kept
-// apart from the launch itself so that it runs before any stream capture
-// (it sets a function attribute and queries occupancy).
+// Launch shape of a batched launch: kernel variant, grid and dynamic shared
+// memory.  Kept apart from the launch itself so that it runs before any
+// stream capture (it sets a function attribute and queries occupancy).
 struct LaunchShape {
+    BatchKernelFn kernel;
     int threads;
     unsigned grid;
     size_t smem;
-    bool learned;
-    int min_blocks;
 };
 
-template <int kThreads, bool LEARNED, int kMinBlocks>
-int shape_for(const BatchArgs &args, int ctas_per_sm, LaunchShape *out)
+// Per-kernel, per-device cache of "dynamic shared memory attribute set +
+// occupancy" (the attribute is a per-device property of each kernel).
+struct KernelCache {
+    static constexpr int kMax = 64;
+    BatchKernelFn fn[kMax] = {};
+    int occ[kMax][KernelSetup::kMaxDevices] = {};
+    int n = 0;
+    std::mutex mu;
+};
+
+int occupancy_of(BatchKernelFn fn, int threads, size_t smem, int *occ)
 {
-    // the warp queues are static shared memory; the learned variant adds
-    // its weights and input rows as dynamic shared memory
-    const size_t smem = LEARNED ? sizeof(LearnedSmem<kThreads>) : 0;
-    static KernelSetup setup;
+    static KernelCache cache;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    if (dev < 0 || dev >= KernelSetup::kMaxDevices)
+        return cuda_fail(cudaErrorInvalidDevice);
+    std::lock_guard<std::mutex> lock(cache.mu);
+    int k = 0;
+    while (k < cache.n && cache.fn[k] != fn)
+        ++k;
+    if (k == cache.n) {
+        if (cache.n == KernelCache::kMax)
+            return cuda_fail(cudaErrorInvalidConfiguration);
+        cache.fn[cache.n++] = fn;
+    }
+    if (cache.occ[k][dev] == 0) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return cuda_fail(e);
+        int o = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, threads, smem);
+        if (e != cudaSuccess)
+            return cuda_fail(e);
+        if (o < 1)
+            return cuda_fail(cudaErrorInvalidConfiguration);
+        cache.occ[k][dev] = o;
+    }
+    *occ = cache.occ[k][dev];
+    return RBSM_OK;
+}
+
+template <int kThreads, bool LEARNED, int kMinBlocks>
+BatchKernelFn kernel_for(int umode)
+{
+    if (kThreads == 256 && kMinBlocks == 4)
+        return batch_kernel_256_4(LEARNED, umode);
+    if (kThreads == 256 && kMinBlocks == 3)
+        return batch_kernel_256_3(umode);
+    return batch_kernel_misc(kThreads, LEARNED);
+}
+
+template <int kThreads, bool LEARNED, int kMinBlocks>
+int shape_for(const BatchArgs &args, int ctas_per_sm, int umode, LaunchShape *out)
+{
+    const size_t smem = batch_smem_bytes<kThreads, LEARNED>();
+    const BatchKernelFn fn = kernel_for<kThreads, LEARNED, kMinBlocks>(umode);
     int occ = 0;
-    int rc = setup.get(batch_kernel<kThreads, LEARNED, kMinBlocks>, kThreads, smem, &occ);
+    int rc = occupancy_of(fn, kThreads, smem, &occ);
     if (rc != RBSM_OK)
         return rc;
     if (ctas_per_sm > 0 && ctas_per_sm < occ)
@@ -295,52 +102,47 @@ int shape_for(const BatchArgs &args, int ctas_per_sm, LaunchShape *out)
         grid = blocks_needed;
     if (grid < 1)
         grid = 1;
-    *out = LaunchShape{kThreads, (unsigned)grid, smem, LEARNED, kMinBlocks};
+    *out = LaunchShape{fn, kThreads, (unsigned)grid, smem};
     return RBSM_OK;
 }
 
-// Kernel variant for a launch request.  At 256 threads, asking for 5 or 6
-// CTAs per SM selects the variant whose registers are sized for that many
-// (fewer registers per thread, more warps to hide gather latency).
+// The (mode, codes) pair shared by every job, as UMODE, or 0 when they differ.
+int uniform_mode(const BatchArgs &a)
+{
+    const int m = a.jobs[0].mode, c = a.jobs[0].codes_on;
+    for (int k = 1; k < a.n_jobs; ++k)
+        if (a.jobs[k].mode != m || a.jobs[k].codes_on != c)
+            return 0;
+    return 2 * m + c - 1;
+}
+
+// Kernel variant for a launch request.  At 256 threads, asking for 3 CTAs
+// per SM selects the variant whose registers are sized for 3 (80 per
+// thread instead of 64); the specialisations for a batch-uniform mode exist
+// for the 256-thread shapes.
 int launch_shape(const BatchArgs &args, int threads, int ctas_per_sm, LaunchShape *out)
 {
     const bool learned = args.mlp != nullptr;
+    const int um = uniform_mode(args);
     if (learned) {
         switch (threads) {
-        case 128: return shape_for<128, true, 8>(args, ctas_per_sm, out);
-        case 512: return shape_for<512, true, 2>(args, ctas_per_sm, out);
-        default: return shape_for<256, true, 4>(args, ctas_per_sm, out);
+        case 128: return shape_for<128, true, 8>(args, ctas_per_sm, 0, out);
+        case 512: return shape_for<512, true, 2>(args, ctas_per_sm, 0, out);
+        default: return shape_for<256, true, 4>(args, ctas_per_sm, um, out);
         }
     }
     switch (threads) {
-    case 128: return shape_for<128, false, 8>(args, ctas_per_sm, out);
-    case 512: return shape_for<512, false, 2>(args, ctas_per_sm, out);
+    case 128: return shape_for<128, false, 8>(args, ctas_per_sm, 0, out);
+    case 512: return shape_for<512, false, 2>(args, ctas_per_sm, 0, out);
     default:
-        if (ctas_per_sm >= 6) return shape_for<256, false, 6>(args, ctas_per_sm, out);
-        if (ctas_per_sm == 5) return shape_for<256, false, 5>(args, ctas_per_sm, out);
-        return shape_for<256, false, 4>(args, ctas_per_sm, out);
+        if (ctas_per_sm == 3) return shape_for<256, false, 3>(args, ctas_per_sm, um, out);
+        return shape_for<256, false, 4>(args, ctas_per_sm, um, out);
     }
 }
 
 int launch_kernel(const BatchArgs &args, const LaunchShape &sh, cudaStream_t stream)
 {
-    const unsigned g = sh.grid;
-    const size_t m = sh.smem;
-    if (sh.learned) {
-        switch (sh.threads) {
-        case 128: batch_kernel<128, true, 8><<<g, 128, m, stream>>>(args); break;
-        case 512: batch_kernel<512, true, 2><<<g, 512, m, stream>>>(args); break;
-        default: batch_kernel<256, true, 4><<<g, 256, m, stream>>>(args); break;
-        }
-    } else {
-        switch (sh.threads * 16 + sh.min_blocks) {
-        case 128 * 16 + 8: batch_kernel<128, false, 8><<<g, 128, m, stream>>>(args); break;
-        case 512 * 16 + 2: batch_kernel<512, false, 2><<<g, 512, m, stream>>>(args); break;
-        case 256 * 16 + 6: batch_kernel<256, false, 6><<<g, 256, m, stream>>>(args); break;
-        case 256 * 16 + 5: batch_kernel<256, false, 5><<<g, 256, m, stream>>>(args); break;
-        default: batch_kernel<256, false, 4><<<g, 256, m, stream>>>(args); break;
-        }
-    }
+    sh.kernel<<<sh.grid, sh.threads, sh.smem, stream>>>(args);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return cuda_fail(e);
@@ -496,7 +298,7 @@ int rbsm_batch_graph_create(const rbsm_batch *batch, void *workspace, size_t wor
     if ((rc = rbsm::check_workspace(workspace, workspace_bytes)) != RBSM_OK)
         return rc;
     rbsm::bind_workspace(args, workspace);
-    rbsm::LaunchShape sh{256, 1, 0};
+    rbsm::LaunchShape sh{nullptr, 256, 1, 0};
     if (args.total_tiles > 0 && (rc = rbsm::launch_shape(args, threads, batch->ctas_per_sm, &sh)) != RBSM_OK)
         return rc;
     cudaStream_t s = nullptr;
@@ -583,7 +385,7 @@ int rbsm_batch_autotune(const rbsm_batch *batch, void *workspace, size_t workspa
         return rbsm::cuda_fail(e);
     }
     // candidate (CTA size, CTAs per SM); 0 = the variant's occupancy limit
-    const int cand[][2] = {{128, 0}, {256, 2}, {256, 3}, {256, 0}, {256, 5}, {256, 6}, {512, 1}, {512, 0}};
+    const int cand[][2] = {{128, 0}, {256, 2}, {256, 3}, {256, 0}, {512, 1}, {512, 0}};
     const int n_cand = (int)(sizeof(cand) / sizeof(cand[0]));
     for (int ci = 0; ci < n_cand && rc == RBSM_OK; ++ci) {
         {

@@ -1,0 +1,288 @@
+// Device side of the batched launch: descriptors, per-warp queues, the
+// learned drain and the batch_kernel template.  Its instantiations are
+// spread over rbsm_batch_inst_*.cu so that they compile in parallel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "rbsm.h"
+#include "rbsm_device.cuh"
+#include "rbsm_mlp.cuh"
+
+namespace rbsm {
+
+struct BatchJobDev {
+    const float *x, *y, *z;
+    float *sil, *fil;
+    uint16_t *codes;
+    long long n;
+    long long tile_start;        // first work item of the job
+    int map;
+    int mode;                    // 1, 2, 3
+    int vec;                     // all planes 16-byte aligned
+    int codes_on;
+};
+
+// Passed by value as a __grid_constant__ kernel parameter (about 21 KB,
+// inside the 32 KB parameter space), so no descriptor copy to the device
+// is needed and the launch can be captured into a CUDA graph as is.
+struct BatchArgs {
+    MapDev maps[RBSM_BATCH_MAX_MAPS];
+    BatchJobDev jobs[RBSM_BATCH_MAX_JOBS];
+    int n_jobs;
+    int max_dist;
+    long long total_tiles;
+    unsigned long long *counter;
+    int *status;
+    const void *mlp;                 // surrogate state block or nullptr
+    float tau;                       // guard: largest accepted error estimate
+    unsigned long long *stats;       // [0] surrogate answers, [1] fallbacks
+};
+
+constexpr size_t kWorkspaceBytes = 256;
+constexpr int kChunkTiles = 8;       // warp tiles per claim of the work counter
+
+__device__ __forceinline__ int find_job(const BatchArgs &a, long long tile)
+{
+    int lo = 0, hi = a.n_jobs - 1;    // last job whose first tile <= tile
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.jobs[mid].tile_start <= tile)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ WarpTileIO job_tile(const BatchJobDev &J, int job, long long tile)
+{
+    WarpTileIO t;
+    t.x = J.x; t.y = J.y; t.z = J.z; t.sil = J.sil; t.fil = J.fil; t.codes = J.codes;
+    t.first = (tile - J.tile_start) * kWarpTile;
+    const long long left = J.n - t.first;
+    t.count = left < kWarpTile ? (int)left : kWarpTile;
+    t.job = job;
+    t.vec = J.vec && t.count == kWarpTile;
+    return t;
+}
+
+// Job table of a batched launch, for the deferred edge answers.
+struct BatchJobs {
+    const BatchArgs *a;
+    __device__ __forceinline__ JobOut operator()(int j) const
+    {
+        const BatchJobDev &J = a->jobs[j];
+        return JobOut{a->maps[J.map], J.sil, J.fil, J.codes_on ? J.codes : nullptr, J.mode};
+    }
+};
+
+// Shared memory of the learned variant: the network's weights and, per
+// warp, the 32 input rows and 32 outputs of one round of edge fragments.
+template <int kThreads>
+struct LearnedSmem {
+    mlp::SmemWeights w;
+    uint16_t feat[kThreads / 32][32 * mlp::kIn];
+    float out[kThreads / 32][32 * mlp::kOut];
+};
+
+// Drain rounds of up to 32 queued edge fragments with the surrogate: each
+// lane gathers its fragment's 5x5 features into one input row, the warp runs
+// the network on the 32 rows (two m16 tiles on the tensor cores), and each
+// fragment whose error estimate is within the guard takes the estimate,
+// clamped to [0, 1]; the others (and every fragment of a job that is not in
+// FILTER mode) take the exact walk.
+template <typename Jobs, int kThreads>
+__device__ __forceinline__ void drain_queue_learned(const Jobs &jobs, WarpQueue &wq, int &count, int max_dist,
+                                                    bool all, LearnedSmem<kThreads> &ls, int warp, float tau,
+                                                    unsigned long long *stats)
+{
+    const unsigned lane = lane_id();
+    const int g = lane >> 2, t = lane & 3;
+    uint16_t *feat = ls.feat[warp];
+    float *yout = ls.out[warp];
+    while (count >= 32 || (all && count > 0)) {
+        __syncwarp();
+        const int base = count >= 32 ? count - 32 : 0;
+        const int k = base + (int)lane;
+        const bool valid = k < count;
+        EdgeEntry q{0.0f, 0.0f, 0.0f, 0u, 0};
+        JobOut o{};
+        if (valid) {
+            q = wq.q[k];
+            o = jobs((int)(q.bits_job >> 8));
+        }
+        const bool use_net = valid && o.mode == 2;
+        if (use_net) {
+            uint32_t bits;
+            float fx, fy, gap;
+            fragment_features(o.map, q.x, q.y, q.z, bits, fx, fy, gap);
+            mlp::write_input_row(feat + lane * mlp::kIn, bits, fx, fy, gap);
+        } else {
+            uint4 *row = reinterpret_cast<uint4 *>(feat + lane * mlp::kIn);
+#pragma unroll
+            for (int w4 = 0; w4 < mlp::kIn / 8; ++w4)
+                row[w4] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            uint32_t xa[2][4];
+            mlp::load_a(feat, mlp::kIn, mt * 16, 0, lane, xa[0]);
+            mlp::load_a(feat, mlp::kIn, mt * 16, 1, lane, xa[1]);
+            mlp::HiddenFrags h1, h2;
+            uint32_t m1, m2;
+            mlp::layer(xa, 2, ls.w.w1t, mlp::kIn, ls.w.b1, lane, h1, m1);
+            mlp::layer(h1.a, 4, ls.w.w2t, mlp::kHid, ls.w.b2, lane, h2, m2);
+            float y[4];
+            mlp::output_layer(h2, ls.w, lane, y);
+            if (t == 0) {
+                yout[(mt * 16 + g) * 2] = y[0];
+                yout[(mt * 16 + g) * 2 + 1] = y[1];
+                yout[(mt * 16 + g + 8) * 2] = y[2];
+                yout[(mt * 16 + g + 8) * 2 + 1] = y[3];
+            }
+        }
+        __syncwarp();
+        bool accepted = false;
+        if (use_net) {
+            const float v = yout[lane * 2], e = yout[lane * 2 + 1];
+            accepted = e <= tau && v == v;          // a NaN estimate never passes
+            if (accepted) {
+                const float vc = v < 0.0f ? 0.0f : (v > 1.0f ? 1.0f : v);
+                o.fil[q.idx] = vc;
+                if (o.codes) {
+                    const uint32_t bits = q.bits_job & 0x1fu;
+                    o.codes[q.idx] = (uint16_t)((bits >> 1) | ((1u - (bits & 1u)) << 4) | (1u << 10));
+                }
+            }
+        }
+        if (valid && !accepted)
+            resolve_entry(o, q, max_dist);
+        const unsigned acc_mask = __ballot_sync(0xffffffffu, accepted);
+        const unsigned fb_mask = __ballot_sync(0xffffffffu, use_net && !accepted);
+        if (lane == 0 && (acc_mask | fb_mask)) {
+            atomicAdd(&stats[0], (unsigned long long)__popc(acc_mask));
+            atomicAdd(&stats[1], (unsigned long long)__popc(fb_mask));
+        }
+        __syncwarp();
+        count = base;
+    }
+}
+
+template <int kThreads, bool LEARNED>
+struct BatchSmem {
+    WarpQueue queue[kThreads / 32];
+};
+
+template <int kThreads, bool LEARNED>
+constexpr size_t batch_smem_bytes()
+{
+    return sizeof(BatchSmem<kThreads, LEARNED>) + (LEARNED ? sizeof(LearnedSmem<kThreads>) : 0);
+}
+
+// Persistent warps claim chunks of kChunkTiles warp tiles from the work
+// counter (one atomic per 1024 fragments).  The claim of the next chunk is
+// issued when the current one starts, and its value is read only when the
+// warp gets there, so the atomic's latency hides behind eight tiles of work.
+// While a warp works on one tile, the loads of its next tile's coordinates
+// are in flight (register double buffering).  Consecutive claims are
+// consecutive tiles of the job list, so warps working at the same time
+// share the L2 footprint of one region of one map.
+//
+// UMODE 0: each job's mode and codes flag are read at run time; UMODE
+// 2 * mode + codes - 1 (1..6): every job of the launch has that pair, which
+// keeps one specialisation of the classification in the loop (the run-time
+// dispatch inlines all six and costs registers).
+template <int kThreads, bool LEARNED, int kMinBlocks, int UMODE>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const __grid_constant__ BatchArgs a)
+{
+    constexpr int kFixedMode = (UMODE + 1) / 2;
+    constexpr bool kFixedCodes = ((UMODE + 1) % 2) == 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto &bs = *reinterpret_cast<BatchSmem<kThreads, LEARNED> *>(smem_raw);
+    auto &ls = *reinterpret_cast<LearnedSmem<kThreads> *>(smem_raw + sizeof(BatchSmem<kThreads, LEARNED>));
+    const unsigned lane = lane_id();
+    const int warp = threadIdx.x >> 5;
+    if (LEARNED) {
+        const mlp::State st = mlp::state_of(const_cast<void *>(a.mlp));
+        for (int k = threadIdx.x; k < mlp::kW1tElems; k += kThreads) ls.w.w1t[k] = st.w1t[k];
+        for (int k = threadIdx.x; k < mlp::kW2tElems; k += kThreads) ls.w.w2t[k] = st.w2t[k];
+        for (int k = threadIdx.x; k < mlp::kW3tElems; k += kThreads) ls.w.w3t[k] = st.w3t[k];
+        for (int k = threadIdx.x; k < mlp::kHid; k += kThreads) {
+            ls.w.b1[k] = st.master[mlp::kOffB1 + k];
+            ls.w.b2[k] = st.master[mlp::kOffB2 + k];
+        }
+        for (int k = threadIdx.x; k < mlp::kOutPad; k += kThreads)
+            ls.w.b3[k] = k < mlp::kOut ? st.master[mlp::kOffB3 + k] : 0.0f;
+        __syncthreads();
+    }
+    WarpQueue &wq = bs.queue[warp];
+    const long long total = a.total_tiles;
+    unsigned long long claim = 0;
+    if (lane == 0)
+        claim = atomicAdd(a.counter, 1ull);
+    long long tile = (long long)__shfl_sync(0xffffffffu, claim, 0) * kChunkTiles;
+    if (tile >= total)
+        return;
+    if (lane == 0)
+        claim = atomicAdd(a.counter, 1ull);      // next chunk, read later
+    int in_chunk = 0;
+    int job = find_job(a, tile);
+    WarpTileIO t = job_tile(a.jobs[job], job, tile);
+    LaneCoords c;
+    load_tile(t, lane, c);
+    const BatchJobs jobs{&a};
+    int queued = 0;
+    for (;;) {
+        long long nt;
+        if (in_chunk + 1 < kChunkTiles) {
+            nt = tile + 1;
+            in_chunk += 1;
+        } else {
+            nt = (long long)__shfl_sync(0xffffffffu, claim, 0) * kChunkTiles;
+            in_chunk = 0;
+            if (nt < total && lane == 0)
+                claim = atomicAdd(a.counter, 1ull);
+        }
+        const bool more = nt < total;
+        int njob = job;
+        WarpTileIO tn;
+        LaneCoords cn;
+        if (more) {
+            njob = find_job(a, nt);
+            tn = job_tile(a.jobs[njob], njob, nt);
+            load_tile(tn, lane, cn);           // next tile's loads fly during this tile
+        }
+        const BatchJobDev &J = a.jobs[job];
+        if (UMODE == 0)
+            classify_warp_tile_rt(J.mode, J.codes_on != 0, a.maps[J.map], t, c, wq, queued);
+        else
+            classify_warp_tile<kFixedMode ? kFixedMode : 1, kFixedCodes>(a.maps[J.map], t, c, wq, queued);
+        if (LEARNED)
+            drain_queue_learned<BatchJobs, kThreads>(jobs, wq, queued, a.max_dist, false, ls, warp, a.tau, a.stats);
+        else
+            drain_queue<BatchJobs, kFixedMode>(jobs, wq, queued, a.max_dist, false);
+        if (!more)
+            break;
+        tile = nt;
+        job = njob;
+        t = tn;
+        c = cn;
+    }
+    if (LEARNED)
+        drain_queue_learned<BatchJobs, kThreads>(jobs, wq, queued, a.max_dist, true, ls, warp, a.tau, a.stats);
+    else
+        drain_queue<BatchJobs, kFixedMode>(jobs, wq, queued, a.max_dist, true);
+}
+
+using BatchKernelFn = void (*)(BatchArgs);
+
+// Kernel pointers of the instantiations (one function per translation unit).
+BatchKernelFn batch_kernel_256_4(bool learned, int umode);
+BatchKernelFn batch_kernel_256_3(int umode);
+BatchKernelFn batch_kernel_misc(int threads, bool learned);
+
+}  // namespace rbsm

@@ -324,11 +324,11 @@ __device__ __forceinline__ void resolve_edge(const MapDev &m, float x, float y, 
 constexpr int kWarpTile = 32 * kPerThread;   // 128 fragments
 constexpr int kQueueCap = kWarpTile + 32;    // < 32 left over + one tile
 
-// One deferred edge fragment (24 bytes).
+// One deferred edge fragment (20 bytes).
 struct EdgeEntry {
     float x, y, z;
     uint32_t bits_job;       // s0 | d4 << 1 (5 bits) | job << 8
-    long long idx;           // fragment index within the job
+    uint32_t idx;            // fragment index within the job (fragment sets hold < 2^31)
 };
 
 struct WarpQueue {
@@ -386,12 +386,15 @@ __device__ __forceinline__ void load_tile(const WarpTileIO &t, unsigned lane, La
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 // Walk, normalise and answer one deferred edge fragment; write its answers.
+// FIXED_MODE 1..3 when every job of the launch has that mode, 0 to read it
+// from the job.
+template <int FIXED_MODE = 0>
 __device__ __forceinline__ void resolve_entry(const JobOut &o, const EdgeEntry &q, int max_dist)
 {
     const uint32_t bits = q.bits_job & 0x1fu;
     const uint32_t d4 = bits >> 1, s0 = bits & 1u;
     FragResult r{0.0f, 0.0f, (uint16_t)(d4 | ((1u - s0) << 4))};
-    switch (o.mode) {
+    switch (FIXED_MODE ? FIXED_MODE : o.mode) {
     case 1: resolve_edge<1>(o.map, q.x, q.y, q.z, bits, max_dist, r); break;
     case 2: resolve_edge<2>(o.map, q.x, q.y, q.z, bits, max_dist, r); break;
     default: resolve_edge<3>(o.map, q.x, q.y, q.z, bits, max_dist, r); break;
@@ -404,7 +407,7 @@ __device__ __forceinline__ void resolve_entry(const JobOut &o, const EdgeEntry &
 // Drain full rounds of 32 queued edge fragments (or everything when
 // `all`).  `jobs(job)` returns the JobOut of a job.  The count is uniform
 // across the warp.
-template <typename Jobs>
+template <typename Jobs, int FIXED_MODE = 0>
 __device__ __forceinline__ void drain_queue(const Jobs &jobs, WarpQueue &wq, int &count, int max_dist, bool all)
 {
     const unsigned lane = lane_id();
@@ -414,7 +417,7 @@ __device__ __forceinline__ void drain_queue(const Jobs &jobs, WarpQueue &wq, int
         const int k = base + (int)lane;
         if (k < count) {
             const EdgeEntry q = wq.q[k];
-            resolve_entry(jobs((int)(q.bits_job >> 8)), q, max_dist);
+            resolve_entry<FIXED_MODE>(jobs((int)(q.bits_job >> 8)), q, max_dist);
         }
         __syncwarp();                      // entries read before they are overwritten
         count = base;
@@ -459,7 +462,7 @@ __device__ __forceinline__ void classify_warp_tile(const MapDev &m, const WarpTi
             q.y = c.y[e];
             q.z = c.z[e];
             q.bits_job = bits[e] | ((uint32_t)t.job << 8);
-            q.idx = t.first + s;
+            q.idx = (uint32_t)(t.first + s);
         }
         count += __popc(mask);
     }

@@ -34,7 +34,7 @@ int check_map(const rbsm_map *m)
 
 int check_frags(const rbsm_frags *f)
 {
-    if (!f || f->n < 0)
+    if (!f || f->n < 0 || f->n > RBSM_MAX_FRAGMENTS)
         return RBSM_ERR_ARG;
     if (f->n > 0 && (!f->x || !f->y || !f->z))
         return RBSM_ERR_ARG;
