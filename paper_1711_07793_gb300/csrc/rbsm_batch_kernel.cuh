@@ -231,6 +231,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const __gri
         claim = atomicAdd(a.counter, 1ull);      // next chunk, read later
     int in_chunk = 0;
     int job = find_job(a, tile);
+    // tiles [job_lo, job_hi) belong to `job`: the search runs only when a
+    // tile falls outside the current job
+    long long job_lo = a.jobs[job].tile_start;
+    long long job_hi = job + 1 < a.n_jobs ? a.jobs[job + 1].tile_start : total;
     WarpTileIO t = job_tile(a.jobs[job], job, tile);
     LaneCoords c;
     load_tile(t, lane, c);
@@ -252,7 +256,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const __gri
         WarpTileIO tn;
         LaneCoords cn;
         if (more) {
-            njob = find_job(a, nt);
+            if (nt < job_lo || nt >= job_hi) {
+                njob = find_job(a, nt);
+                job_lo = a.jobs[njob].tile_start;
+                job_hi = njob + 1 < a.n_jobs ? a.jobs[njob + 1].tile_start : total;
+            }
             tn = job_tile(a.jobs[njob], njob, nt);
             load_tile(tn, lane, cn);           // next tile's loads fly during this tile
         }
