@@ -75,7 +75,7 @@ struct BatchJobs {
     __device__ __forceinline__ JobOut operator()(int j) const
     {
         const BatchJobDev &J = a->jobs[j];
-        return JobOut{a->maps[J.map], J.sil, J.fil, J.codes_on ? J.codes : nullptr, J.mode};
+        return JobOut{a->maps[J.map], J.x, J.y, J.z, J.sil, J.fil, J.codes_on ? J.codes : nullptr, J.mode};
     }
 };
 
@@ -108,7 +108,7 @@ __device__ __forceinline__ void drain_queue_learned(const Jobs &jobs, WarpQueue 
         const int base = count >= 32 ? count - 32 : 0;
         const int k = base + (int)lane;
         const bool valid = k < count;
-        EdgeEntry q{0.0f, 0.0f, 0.0f, 0u, 0};
+        EdgeEntry q{0u, 0u};
         JobOut o{};
         if (valid) {
             q = wq.q[k];
@@ -118,7 +118,7 @@ __device__ __forceinline__ void drain_queue_learned(const Jobs &jobs, WarpQueue 
         if (use_net) {
             uint32_t bits;
             float fx, fy, gap;
-            fragment_features(o.map, q.x, q.y, q.z, bits, fx, fy, gap);
+            fragment_features(o.map, __ldg(o.x + q.idx), __ldg(o.y + q.idx), __ldg(o.z + q.idx), bits, fx, fy, gap);
             mlp::write_input_row(feat + lane * mlp::kIn, bits, fx, fy, gap);
         } else {
             uint4 *row = reinterpret_cast<uint4 *>(feat + lane * mlp::kIn);

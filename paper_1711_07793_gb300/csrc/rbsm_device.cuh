@@ -324,11 +324,13 @@ __device__ __forceinline__ void resolve_edge(const MapDev &m, float x, float y, 
 constexpr int kWarpTile = 32 * kPerThread;   // 128 fragments
 constexpr int kQueueCap = kWarpTile + 32;    // < 32 left over + one tile
 
-// One deferred edge fragment (20 bytes).
+// One deferred edge fragment (8 bytes): which fragment, and what its
+// classification found.  The drain reads the fragment's x, y, z again (edge
+// fragments are a few percent of the stream, so keeping the queue small and
+// the shared memory free for the L1 cache pays more).
 struct EdgeEntry {
-    float x, y, z;
-    uint32_t bits_job;       // s0 | d4 << 1 (5 bits) | job << 8
     uint32_t idx;            // fragment index within the job (fragment sets hold < 2^31)
+    uint32_t bits_job;       // s0 | d4 << 1 (5 bits) | job << 8
 };
 
 struct WarpQueue {
@@ -351,9 +353,10 @@ struct WarpTileIO {
     bool vec;                // count == kWarpTile and every plane 16-byte aligned
 };
 
-// Output side of a job, for the deferred answers.
+// A job as the deferred answers need it: its map, its fragments, its outputs.
 struct JobOut {
     MapDev map;
+    const float *x, *y, *z;
     float *sil, *fil;
     uint16_t *codes;
     int mode;
@@ -394,10 +397,11 @@ __device__ __forceinline__ void resolve_entry(const JobOut &o, const EdgeEntry &
     const uint32_t bits = q.bits_job & 0x1fu;
     const uint32_t d4 = bits >> 1, s0 = bits & 1u;
     FragResult r{0.0f, 0.0f, (uint16_t)(d4 | ((1u - s0) << 4))};
+    const float x = __ldg(o.x + q.idx), y = __ldg(o.y + q.idx), z = __ldg(o.z + q.idx);
     switch (FIXED_MODE ? FIXED_MODE : o.mode) {
-    case 1: resolve_edge<1>(o.map, q.x, q.y, q.z, bits, max_dist, r); break;
-    case 2: resolve_edge<2>(o.map, q.x, q.y, q.z, bits, max_dist, r); break;
-    default: resolve_edge<3>(o.map, q.x, q.y, q.z, bits, max_dist, r); break;
+    case 1: resolve_edge<1>(o.map, x, y, z, bits, max_dist, r); break;
+    case 2: resolve_edge<2>(o.map, x, y, z, bits, max_dist, r); break;
+    default: resolve_edge<3>(o.map, x, y, z, bits, max_dist, r); break;
     }
     if (o.mode & 1) o.sil[q.idx] = r.sil;
     if (o.mode & 2) o.fil[q.idx] = r.fil;
@@ -457,12 +461,8 @@ __device__ __forceinline__ void classify_warp_tile(const MapDev &m, const WarpTi
         const int s = t.vec ? (int)(kPerThread * lane) + e : (int)lane + 32 * e;
         const unsigned mask = __ballot_sync(0xffffffffu, edge[e]);
         if (edge[e]) {
-            EdgeEntry &q = wq.q[count + __popc(mask & below)];
-            q.x = c.x[e];
-            q.y = c.y[e];
-            q.z = c.z[e];
-            q.bits_job = bits[e] | ((uint32_t)t.job << 8);
-            q.idx = (uint32_t)(t.first + s);
+            wq.q[count + __popc(mask & below)] =
+                EdgeEntry{(uint32_t)(t.first + s), bits[e] | ((uint32_t)t.job << 8)};
         }
         count += __popc(mask);
     }

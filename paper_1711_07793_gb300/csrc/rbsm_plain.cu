@@ -102,7 +102,7 @@ plain_kernel(const MapDev m, const float *__restrict__ x, const float *__restric
     long long tile = (long long)blockIdx.x * kWarps + warp;
     if (tile >= tiles)
         return;
-    const PlainJobs jobs{JobOut{m, sil, fil, CODES ? codes : nullptr, MODE}};
+    const PlainJobs jobs{JobOut{m, x, y, z, sil, fil, CODES ? codes : nullptr, MODE}};
     auto io_of = [&](long long tl) {
         WarpTileIO t;
         t.x = x; t.y = y; t.z = z; t.sil = sil; t.fil = fil; t.codes = codes;
