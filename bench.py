@@ -36,7 +36,8 @@ UNIT = "Gfragments/s"
 BYTES_PER_FRAGMENT = 12 + 4 + 4     # x, y, z in; silhouette and filter visibility out
 BYTES_PER_TEXEL = 4                 # each unique centre texel read once
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["paper_1711_07793_gb300/csrc/rbsm_device.cuh", "paper_1711_07793_gb300/csrc/rbsm_batch.cu"]
+KERNEL_SOURCES = ["paper_1711_07793_gb300/csrc/rbsm_device.cuh", "paper_1711_07793_gb300/csrc/rbsm_batch_kernel.cuh",
+                  "paper_1711_07793_gb300/csrc/rbsm_batch.cu"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "batch_kernel_c5_traffic.md")
 
 
@@ -55,6 +56,10 @@ def parse_args(argv=None):
     p.add_argument("--guard-tau", type=float, default=0.05, help="surrogate guard (largest accepted error estimate)")
     p.add_argument("--texture", choices=["on", "off"], default="on",
                    help="read each map's four-neighbourhood with texture gathers (rbsm_map_texture_create)")
+    p.add_argument("--graph", choices=["on", "off"], default="on",
+                   help="replay the batched launch as a CUDA graph (rbsm_batch_graph_*)")
+    p.add_argument("--autotune", choices=["on", "off"], default="on",
+                   help="pick the launch shape with rbsm_batch_autotune before timing")
     p.add_argument("--tile-threads", type=int, default=0)
     p.add_argument("--ctas-per-sm", type=int, default=0)
     return p.parse_args(argv)
@@ -288,10 +293,21 @@ def run_ours(args, rank, world, local_rank):
     batch = api.Batch(texs or maps, jobs, tile_threads=args.tile_threads, ctas_per_sm=args.ctas_per_sm)
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
+    tuning = None
+    if args.autotune == "on" and not args.tile_threads and not args.ctas_per_sm:
+        tuning = api.rbsm_batch_autotune(batch, repeats=3, cache=None)
+        torch.cuda.synchronize()
+    graph = api.BatchGraph(batch) if args.graph == "on" else None
+
+    def step():
+        if graph is not None:
+            graph.launch()
+        else:
+            api.rbsm_batch_run(batch)
 
     # warm-up, then exactly K timed steps, one CUDA event pair per launch
     for _ in range(args.warmup):
-        api.rbsm_batch_run(batch)
+        step()
     sampler = ClockSampler(smi_gpu_id(local_rank))
     sampler.start()
     time.sleep(0.5)
@@ -302,7 +318,7 @@ def run_ours(args, rank, world, local_rank):
     t0 = time.time()
     for k in range(args.steps):
         starts[k].record(stream)
-        api.rbsm_batch_run(batch)
+        step()
         ends[k].record(stream)
     torch.cuda.synchronize()
     t1 = time.time()
@@ -335,7 +351,7 @@ def run_ours(args, rank, world, local_rank):
             for k in range(frames):
                 maps[k].copy_(host[k]["depth"], non_blocking=True)
                 xyz[k].copy_(host[k]["xyz"], non_blocking=True)
-            api.rbsm_batch_run(batch)
+            step()
             for k in range(frames):
                 out_sil[k].copy_(jobs[k].vis_silhouette, non_blocking=True)
                 out_fil[k].copy_(jobs[k].vis_filter, non_blocking=True)
@@ -373,12 +389,14 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "inputs larger than L2 (%.1f GB per step), no flush" % (
                        sum(h["depth"].numel() * 4 + h["xyz"].numel() * 4 for h in host) / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "tile_threads": args.tile_threads or 256, "ctas_per_sm": args.ctas_per_sm or "occupancy",
+                   "tile_threads": batch.desc.tile_threads or 256,
+                   "ctas_per_sm": batch.desc.ctas_per_sm or "occupancy",
+                   "autotune": tuning, "cuda_graph": graph is not None,
                    "neighbourhood": "texture gathers" if texs else "plain loads"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
                      else "fallback 6800 GB/s",
-                     "traffic": traffic, "kernel": "rbsm::batch_kernel<256>",
+                     "traffic": traffic, "kernel": "rbsm::batch_kernel",
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "mean_launch_ms": mean_launch_ms, "min_launch_ms": min(launch_ms)},
         "e2e": e2e,
