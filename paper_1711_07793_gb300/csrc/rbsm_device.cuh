@@ -54,54 +54,85 @@ __device__ __forceinline__ void texel_coord(float x, int size, int &t, float &f)
     t = (int)c;
 }
 
-// Listing 3 along x.  A texel of the walk continues the edge when it keeps
-// the fragment's shadow-test result and shares a discontinuity direction
-// with the fragment.  Along x only the +-y directions can be shared: the
-// walk's texel has the same result as the texel it came from (so no shared
-// direction back along the walk), and the fragment has no discontinuity in
-// the walking direction (else the first step ends the walk).  Both facts
-// hold with clamp-to-edge addressing too.  Returns +k for an end found at
-// step k, -k for a texel that left the edge, -(max_dist+1) when all steps
-// continued.  The three rows the walk reads are fixed: their addresses are
-// formed once.
-__device__ __forceinline__ int walk_x(const MapDev &m, int i, int j, float pz, int s0,
-                                      bool up, bool down, int di, int max_dist)
+// Listing 3 along one axis, both directions.  A texel of the walk continues
+// the edge when it keeps the fragment's shadow-test result and shares a
+// discontinuity direction with the fragment.  Along x only the +-y
+// directions can be shared: the walk's texel has the same result as the
+// texel it came from (so no shared direction back along the walk), and the
+// fragment has no discontinuity in the walking direction (else the first
+// step ends the walk).  Both facts hold with clamp-to-edge addressing too;
+// along y the same holds with the axes swapped.  A walk returns +k for an
+// end found at step k, -k for a texel that left the edge, -(max_dist+1) when
+// all steps continued: rn for the walk towards lower indices, rp for the
+// walk towards higher ones.
+//
+// The walks read three fixed lines of the map (the row or column of the
+// fragment and its two neighbours): `line` points at the first texel of the
+// fragment's own line, `side_a`/`side_b` at the neighbouring lines that
+// share a direction (use_a/use_b), `stride` is the distance between
+// consecutive texels of a line and `pos`/`last` the fragment's index and the
+// last index along it.  The two directions advance together and every load
+// of a step (of both walks; a finished walk issues none) is in flight before
+// the first test, so a step costs one memory latency.  Loads of later steps
+// are not issued ahead: the extra, mostly wasted, requests cost more than
+// the latency they hide.
+__device__ __forceinline__ void walk_pair(const float *line, const float *side_a, const float *side_b,
+                                          long long stride, int pos, int last, bool use_a, bool use_b,
+                                          float pz, int s0, int max_dist, int &rn, int &rp)
+{
+    rn = 0;
+    rp = 0;
+    for (int k = 1; k <= max_dist; ++k) {
+        const bool an = rn == 0, ap = rp == 0;
+        const long long offn = (long long)max(pos - k, 0) * stride;
+        const long long offp = (long long)min(pos + k, last) * stride;
+        const float zcn = an ? __ldg(line + offn) : 0.0f;
+        const float zan = an && use_a ? __ldg(side_a + offn) : 0.0f;
+        const float zbn = an && use_b ? __ldg(side_b + offn) : 0.0f;
+        const float zcp = ap ? __ldg(line + offp) : 0.0f;
+        const float zap = ap && use_a ? __ldg(side_a + offp) : 0.0f;
+        const float zbp = ap && use_b ? __ldg(side_b + offp) : 0.0f;
+        if (an) {
+            if (shadow_test(pz, zcn) != s0)
+                rn = k;
+            else if (!((use_a && shadow_test(pz, zan) != s0) || (use_b && shadow_test(pz, zbn) != s0)))
+                rn = -k;
+        }
+        if (ap) {
+            if (shadow_test(pz, zcp) != s0)
+                rp = k;
+            else if (!((use_a && shadow_test(pz, zap) != s0) || (use_b && shadow_test(pz, zbp) != s0)))
+                rp = -k;
+        }
+        if (rn != 0 && rp != 0)
+            return;
+    }
+    if (rn == 0)
+        rn = -(max_dist + 1);
+    if (rp == 0)
+        rp = -(max_dist + 1);
+}
+
+// The walks along x from texel (i, j): rows j, j+1 (shared +y) and j-1
+// (shared -y).
+__device__ __forceinline__ void walks_x(const MapDev &m, int i, int j, float pz, int s0,
+                                        bool up, bool down, int max_dist, int &rn, int &rp)
 {
     const float *row = m.depth + (long long)j * m.pitch;
     const float *row_up = m.depth + (long long)min(j + 1, m.height - 1) * m.pitch;
     const float *row_dn = m.depth + (long long)max(j - 1, 0) * m.pitch;
-    const int last = m.width - 1;
-    for (int k = 1; k <= max_dist; ++k) {
-        const int c = min(max(i + k * di, 0), last);
-        if (shadow_test(pz, __ldg(row + c)) != s0)
-            return k;
-        const bool keep = (up && shadow_test(pz, __ldg(row_up + c)) != s0) ||
-                          (down && shadow_test(pz, __ldg(row_dn + c)) != s0);
-        if (!keep)
-            return -k;
-    }
-    return -(max_dist + 1);
+    walk_pair(row, row_up, row_dn, 1, i, m.width - 1, up, down, pz, s0, max_dist, rn, rp);
 }
 
-// Listing 3 along y (only the left/right directions can be shared); the
-// three columns are fixed.
-__device__ __forceinline__ int walk_y(const MapDev &m, int i, int j, float pz, int s0,
-                                      bool left, bool right, int dj, int max_dist)
+// The walks along y from texel (i, j): columns i, i-1 (shared left) and i+1
+// (shared right).
+__device__ __forceinline__ void walks_y(const MapDev &m, int i, int j, float pz, int s0,
+                                        bool left, bool right, int max_dist, int &rn, int &rp)
 {
     const float *col = m.depth + i;
     const float *col_l = m.depth + max(i - 1, 0);
     const float *col_r = m.depth + min(i + 1, m.width - 1);
-    const int last = m.height - 1;
-    for (int k = 1; k <= max_dist; ++k) {
-        const long long off = (long long)min(max(j + k * dj, 0), last) * m.pitch;
-        if (shadow_test(pz, __ldg(col + off)) != s0)
-            return k;
-        const bool keep = (left && shadow_test(pz, __ldg(col_l + off)) != s0) ||
-                          (right && shadow_test(pz, __ldg(col_r + off)) != s0);
-        if (!keep)
-            return -k;
-    }
-    return -(max_dist + 1);
+    walk_pair(col, col_l, col_r, m.pitch, j, m.height - 1, left, right, pz, s0, max_dist, rn, rp);
 }
 
 // Eq. 5 and the normalisation along one axis: the position of the fragment
@@ -234,19 +265,24 @@ template <int MODE, bool CODES>
 __device__ __forceinline__ bool classify(const MapDev &m, float x, float y, float pz,
                                          FragResult &r, uint32_t &bits)
 {
+    if (m.tex) {
+        // Texel coordinates in float (clamp(floor(u)) is an integer-valued
+        // float, exact below 2^24), then two 2x2 gathers (point sampling,
+        // clamp to edge, unnormalised coordinates; the footprint of a gather
+        // at (u, v) is columns u-1, u and rows v-1, v): at (i, j) columns
+        // i-1..i, rows j-1..j; at (i+1, j+1) columns i..i+1, rows j..j+1.
+        // Gather order: x = (lo col, hi row), y = (hi, hi), z = (hi, lo),
+        // w = (lo, lo).
+        const float ci = fminf(fmaxf(floorf(__fmul_rn(x, (float)m.width)), 0.0f), (float)(m.width - 1));
+        const float cj = fminf(fmaxf(floorf(__fmul_rn(y, (float)m.height)), 0.0f), (float)(m.height - 1));
+        const float4 a = tex2Dgather<float4>(m.tex, ci, cj, 0);
+        const float4 b = tex2Dgather<float4>(m.tex, ci + 1.0f, cj + 1.0f, 0);
+        return classify_from<MODE, CODES>(pz, a.y, a.x, b.z, b.x, a.z, r, bits);
+    }
     int i, j;
     float fx, fy;
     texel_coord(x, m.width, i, fx);
     texel_coord(y, m.height, j, fy);
-    if (m.tex) {
-        // two 2x2 gathers (point sampling, clamp to edge, unnormalised
-        // coordinates): at (i, j) the footprint is columns i-1..i, rows
-        // j-1..j; at (i+1, j+1) it is columns i..i+1, rows j..j+1.  Gather
-        // order: x = (lo col, hi row), y = (hi, hi), z = (hi, lo), w = (lo, lo).
-        const float4 a = tex2Dgather<float4>(m.tex, (float)i, (float)j, 0);
-        const float4 b = tex2Dgather<float4>(m.tex, (float)(i + 1), (float)(j + 1), 0);
-        return classify_from<MODE, CODES>(pz, a.y, a.x, b.z, b.x, a.z, r, bits);
-    }
     const float *c = m.depth + (long long)j * m.pitch + i;
     const float zc = __ldg(c);
     const int s0 = shadow_test(pz, zc);
@@ -294,10 +330,11 @@ __device__ __forceinline__ void resolve_edge(const MapDev &m, float x, float y, 
     int s0 = bits & 1;
     bool dl = (bits >> 1) & 1, dr = (bits >> 2) & 1, du = (bits >> 3) & 1, dd = (bits >> 4) & 1;
     // computeFragmentDistanceToSE: the four walks -x, +x, -y, +y
-    int rxn = walk_x(m, i, j, pz, s0, du, dd, -1, max_dist);
-    int rxp = walk_x(m, i, j, pz, s0, du, dd, +1, max_dist);
-    int ryn = walk_y(m, i, j, pz, s0, dl, dr, -1, max_dist);
-    int ryp = walk_y(m, i, j, pz, s0, dl, dr, +1, max_dist);
+    // (with a texture view too: 2x2 gathers that take two steps per fetch
+    // measured slower than these loads)
+    int rxn, rxp, ryn, ryp;
+    walks_x(m, i, j, pz, s0, du, dd, max_dist, rxn, rxp);
+    walks_y(m, i, j, pz, s0, dl, dr, max_dist, ryn, ryp);
     int ex = (rxn > 0) + (rxp > 0);
     int ey = (ryn > 0) + (ryp > 0);
     float nx = axis_position(rxn, rxp, fx);

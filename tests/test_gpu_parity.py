@@ -58,11 +58,22 @@ def assert_parity(vis, codes, ref, mode, where=""):
         assert diff.max(initial=0.0) <= FILTER_TOL, "%s: max |diff| %g" % (where, diff.max())
 
 
-def check_both(api, depth, x, y, z, where, max_dist=16):
+def check_both(api, depth, x, y, z, where, max_dist=16, texture=False):
+    """Both visibility modes against the oracle; with texture=True through a
+    texture view of the map as well (when the device accepts one)."""
+    maps = [("loads", depth)]
+    tex = None
+    if texture:
+        tex = _try_texture(api, dev(depth))
+        if tex is not None:
+            maps.append(("texture", tex))
     for mode in (orc.MODE_SILHOUETTE, orc.MODE_FILTER):
         ref = orc.evaluate(depth, x, y, z, mode, max_dist=max_dist)
-        vis, cod = run_gpu(api, depth, x, y, z, mode, max_dist=max_dist)
-        assert_parity(vis, cod, ref, mode, "%s mode %d" % (where, mode))
+        for name, d in maps:
+            vis, cod = run_gpu(api, d, x, y, z, mode, max_dist=max_dist)
+            assert_parity(vis, cod, ref, mode, "%s %s mode %d" % (where, name, mode))
+    if tex is not None:
+        tex.close()
 
 
 # ------------------------------------------------------------- workloads --
@@ -95,7 +106,7 @@ def test_paper_shapes_on_gpu(api, golden_dir):
         depth = shapes.embed(_inside(rects[shape]["in"], ti + 0.5, tj + 0.5), 32, 12)
         X, Y = shapes.fragment_grid(12, 15, 12, 15, [((a + .5) / 5, (b + .5) / 5) for a in range(5) for b in range(5)])
         x, y = shapes.to_texcoords(X, Y, 32, 32)
-        check_both(api, depth, x, y, np.ones_like(x), "fig3 %s" % shape)
+        check_both(api, depth, x, y, np.ones_like(x), "fig3 %s" % shape, texture=True)
     for run_len in (1, 3, 7, 16):
         for orient in shapes.D4_NAMES:
             mask = shapes.staircase_mask(128, run_len, 8, 40)
@@ -103,7 +114,7 @@ def test_paper_shapes_on_gpu(api, golden_dir):
             X, Y = shapes.fragment_grid(20, 108, 20, 108, [((a + .5) / 4, (b + .5) / 4) for a in range(4) for b in range(4)])
             Xt, Yt = shapes.d4_points(X, Y, 128, orient)
             x, y = shapes.to_texcoords(Xt, Yt, 128, 128)
-            check_both(api, depth, x, y, np.ones_like(x), "stair %d %s" % (run_len, orient))
+            check_both(api, depth, x, y, np.ones_like(x), "stair %d %s" % (run_len, orient), texture=True)
 
 
 # ------------------------------------------------------------- edge cases --
@@ -134,7 +145,7 @@ def test_ragged_sizes(api, n):
 def test_degenerate_and_odd_maps(api, w, h):
     rng = np.random.default_rng(w * 1000 + h)
     depth, x, y, z = _random_case(rng, w, h, 5000)
-    check_both(api, depth, x, y, z, "%dx%d" % (w, h))
+    check_both(api, depth, x, y, z, "%dx%d" % (w, h), texture=True)
 
 
 def test_out_of_range_and_nan_coordinates(api):
@@ -147,11 +158,22 @@ def test_out_of_range_and_nan_coordinates(api):
     check_both(api, depth, x, y, z, "out-of-range")
 
 
-@pytest.mark.parametrize("max_dist", [1, 2, 5, 16, 64, 255])
+@pytest.mark.parametrize("max_dist", [1, 2, 3, 5, 16, 17, 64, 255])
 def test_max_dist(api, max_dist):
+    """Every traversal cap, odd and even (the texture walk takes two steps
+    per fetch), on plain loads and on a texture view."""
     import rbsm_scenes as sc
     f = sc.config1(1)
-    check_both(api, f.depth, f.x, f.y, f.z, "max_dist=%d" % max_dist, max_dist=max_dist)
+    check_both(api, f.depth, f.x, f.y, f.z, "max_dist=%d" % max_dist, max_dist=max_dist, texture=True)
+    for run_len in (1, 2, 3, 16):
+        mask = shapes.staircase_mask(96, run_len, 4, 30)
+        depth = np.where(mask, shapes.BLOCKER, shapes.LIT).astype(np.float32)
+        X, Y = shapes.fragment_grid(10, 86, 10, 86, [(0.25, 0.25), (0.75, 0.6)])
+        x, y = shapes.to_texcoords(X, Y, 96, 96)
+        for tr in (False, True):   # runs along x, then (transposed) along y
+            d, u, v = (np.ascontiguousarray(depth.T), y, x) if tr else (depth, x, y)
+            check_both(api, d, u, v, np.ones_like(x), "stair %d%s max_dist=%d" % (run_len, " T" if tr else "", max_dist),
+                       max_dist=max_dist, texture=True)
 
 
 def test_pitched_map_and_unaligned_planes(api):
