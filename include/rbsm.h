@@ -274,6 +274,70 @@ int rbsm_batch_surrogate_counts(const void *workspace, uint64_t *accepted, uint6
 int rbsm_batch_status(const void *workspace, int *status);
 
 /*
+ * Host-resident batches: the stager (this library's addition; the paper
+ * evaluates fragments where the renderer produced them, on the GPU, and has
+ * no host-side interface).
+ *
+ * rbsm_stager_run takes an rbsm_batch whose maps, fragment planes and
+ * answer planes live in page-locked host memory (cudaHostAlloc or
+ * cudaHostRegister; pageable memory is rejected) and returns the answers
+ * to those host planes.  Per map (in index order) it moves to the device
+ * only what the path can read: the fragment planes of the map's jobs and
+ * the window of the map within h = max_dist + 1 texels of some fragment's
+ * texel.  The shadow test and discontinuity check (Eq. 1, Listing 2) read
+ * one texel around the fragment's texel, each edge traversal (Listing 3) at
+ * most max_dist texels along one row or column and one across it, and the
+ * learned surrogate's 5x5 window two; no read leaves the window, so the
+ * answers are those rbsm_batch_run gives on device copies of the whole
+ * batch, bit for bit.  The window is the bounding box of the jobs' texels
+ * (computed on the device from the staged fragments, with the texel
+ * arithmetic of the kernels) grown by h and clipped to the map; the
+ * texels outside it are never copied.
+ *
+ * Work per map, with no host wait anywhere: copies of the fragment planes
+ * in, the texel bounds, a kernel that copies the window rows in from the
+ * host map, the batched kernel, copies of the answers out.  These run on
+ * the stager's own streams through a ring of device slots, so the copies
+ * in of one map, the kernel of the previous one and the copies out of the
+ * one before overlap.  The call is ordered after the work already enqueued
+ * on `stream`, and `stream` is ordered after the call's last copy out.
+ *
+ * desc: max_fragments = the largest sum of n over the jobs of one map;
+ * max_width / max_height bound every map; slots = device slots in the ring,
+ * 2..4 (0 = 3: in, kernel and out of three maps at once); texture = 1 to
+ * read the staged maps through texture gathers; flags reserved (0).  A slot
+ * holds 22 bytes per fragment (x, y, z, both answers, codes) and one map.
+ * Creation allocates the slots and streams (device memory, driver objects)
+ * and may not run during a stream capture; the calls of one stager must
+ * come from one thread at a time, and a stager is not graph-capturable.
+ *
+ * rbsm_stager_run errors: RBSM_ERR_ARG as for rbsm_batch_run, or a map
+ * descriptor with a texture, a map larger than max_width x max_height, the
+ * jobs of one map holding more than max_fragments fragments, or a plane
+ * that is not page-locked host memory; RBSM_ERR_CUDA when a copy or launch
+ * fails (work already enqueued for earlier maps stays enqueued).
+ * rbsm_stager_stats waits for the stager's work and returns the bytes its
+ * runs copied in (fragment planes and map windows) and out (answers),
+ * summed over every run since creation.  rbsm_stager_status waits for the
+ * stager's work and returns the first RBSM_ERR_* code a kernel recorded in
+ * any slot, or RBSM_OK.
+ */
+typedef struct rbsm_stager_s *rbsm_stager;
+typedef struct {
+    int64_t max_fragments;
+    int32_t max_width;
+    int32_t max_height;
+    int32_t slots;
+    int32_t texture;
+    int32_t flags;
+} rbsm_stager_desc;
+int rbsm_stager_create(const rbsm_stager_desc *desc, rbsm_stager *stager);
+int rbsm_stager_run(rbsm_stager stager, const rbsm_batch *batch, void *stream);
+int rbsm_stager_stats(rbsm_stager stager, int64_t *bytes_in, int64_t *bytes_out);
+int rbsm_stager_status(rbsm_stager stager, int *status);
+int rbsm_stager_destroy(rbsm_stager stager);
+
+/*
  * Learned penumbra surrogate (not in the paper; this library's addition).
  * A 32-64-64-2 perceptron estimates the Listing 5 answer of an edge
  * fragment from its 5x5 shadow-test pattern (bit (dy+2)*5 + (dx+2) set when

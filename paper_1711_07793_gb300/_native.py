@@ -67,6 +67,12 @@ class rbsm_tuning(ctypes.Structure):
                 ("ms", ctypes.c_float), ("candidates", ctypes.c_int32)]
 
 
+class rbsm_stager_desc(ctypes.Structure):
+    _fields_ = [("max_fragments", ctypes.c_int64), ("max_width", ctypes.c_int32),
+                ("max_height", ctypes.c_int32), ("slots", ctypes.c_int32), ("texture", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
 class RBSMError(RuntimeError):
     def __init__(self, fn, code, cuda_error=0):
         msg = "%s failed: %s (%d)" % (fn, status_string(code), code)
@@ -109,6 +115,16 @@ def _declare(lib):
     lib.rbsm_batch_status.argtypes = [vp, _P(ctypes.c_int)]
     lib.rbsm_batch_surrogate_counts.restype = i32
     lib.rbsm_batch_surrogate_counts.argtypes = [vp, _P(ctypes.c_uint64), _P(ctypes.c_uint64)]
+    lib.rbsm_stager_create.restype = i32
+    lib.rbsm_stager_create.argtypes = [_P(rbsm_stager_desc), _P(vp)]
+    lib.rbsm_stager_run.restype = i32
+    lib.rbsm_stager_run.argtypes = [vp, _P(rbsm_batch), vp]
+    lib.rbsm_stager_stats.restype = i32
+    lib.rbsm_stager_stats.argtypes = [vp, _P(ctypes.c_int64), _P(ctypes.c_int64)]
+    lib.rbsm_stager_status.restype = i32
+    lib.rbsm_stager_status.argtypes = [vp, _P(ctypes.c_int)]
+    lib.rbsm_stager_destroy.restype = i32
+    lib.rbsm_stager_destroy.argtypes = [vp]
     lib.rbsm_mlp_state_bytes.restype = ctypes.c_size_t
     lib.rbsm_mlp_state_bytes.argtypes = []
     for name in ("rbsm_mlp_load", "rbsm_mlp_store"):

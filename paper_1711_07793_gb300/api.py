@@ -149,12 +149,13 @@ class Job:
         self.map_index, self.mode = int(map_index), int(mode)
         self.x, self.y, self.z = x, y, z
         n = x.shape[0]
+        pin = not x.is_cuda      # host jobs (Stager) answer into page-locked planes
         if (mode & 1) and vis_silhouette is None:
-            vis_silhouette = torch.empty(n, dtype=torch.float32, device=x.device)
+            vis_silhouette = torch.empty(n, dtype=torch.float32, device=x.device, pin_memory=pin)
         if (mode & 2) and vis_filter is None:
-            vis_filter = torch.empty(n, dtype=torch.float32, device=x.device)
+            vis_filter = torch.empty(n, dtype=torch.float32, device=x.device, pin_memory=pin)
         if codes is True:
-            codes = torch.empty(n, dtype=torch.int16, device=x.device)
+            codes = torch.empty(n, dtype=torch.int16, device=x.device, pin_memory=pin)
         self.vis_silhouette, self.vis_filter, self.codes = vis_silhouette, vis_filter, codes
 
     def desc(self):
@@ -285,3 +286,97 @@ def rbsm_batch_surrogate_counts(batch):
             N.lib().rbsm_batch_surrogate_counts(ctypes.c_void_p(batch.workspace.data_ptr()), ctypes.byref(a),
                                                 ctypes.byref(f)))
     return a.value, f.value
+
+
+def _host_plane(name, t, n=None, dtype=torch.float32):
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype or t.dim() != 1:
+        raise TypeError("%s must be a 1-D %s tensor" % (name, dtype))
+    if n is not None and t.shape[0] != n:
+        raise ValueError("%s has %d elements, expected %d" % (name, t.shape[0], n))
+    if t.numel() == 0:
+        return None
+    if t.is_cuda or not t.is_pinned():
+        raise TypeError("%s must be a page-locked (pinned) CPU tensor" % name)
+    if t.numel() > 1 and t.stride(0) != 1:
+        raise ValueError("%s must be contiguous" % name)
+    if n is not None and t.shape[0] != n:
+        raise ValueError("%s has %d elements, expected %d" % (name, t.shape[0], n))
+    return t.data_ptr()
+
+
+def _host_map_desc(depth):
+    if not isinstance(depth, torch.Tensor) or depth.dtype != torch.float32 or depth.dim() != 2:
+        raise TypeError("depth must be a 2-D float32 tensor")
+    if depth.is_cuda or not depth.is_pinned():
+        raise TypeError("depth must be a page-locked (pinned) CPU tensor")
+    if depth.stride(1) != 1 or depth.stride(0) < depth.shape[1]:
+        raise ValueError("depth rows must be contiguous (pitch >= width)")
+    return N.rbsm_map(depth.data_ptr(), depth.shape[1], depth.shape[0], depth.stride(0), 0)
+
+
+def _host_job_desc(j):
+    n = j.x.shape[0]
+    f = N.rbsm_frags(_host_plane("x", j.x), _host_plane("y", j.y, n), _host_plane("z", j.z, n), n)
+    sil = _host_plane("vis_silhouette", j.vis_silhouette, n) if j.vis_silhouette is not None else None
+    fil = _host_plane("vis_filter", j.vis_filter, n) if j.vis_filter is not None else None
+    cod = None
+    if j.codes is not None:
+        if j.codes.dtype not in (torch.int16, torch.uint16):
+            raise TypeError("codes must be int16 or uint16")
+        cod = _host_plane("codes", j.codes, n, j.codes.dtype)
+    return N.rbsm_job(j.map_index, j.mode, f, sil, fil, cod)
+
+
+class Stager:
+    """Host-resident batches (rbsm_stager_*): shadow maps, fragment planes
+    and answer planes in page-locked host memory (pinned CPU tensors; Job
+    allocates pinned answers for CPU inputs).  Per map the library copies
+    in the fragment planes and only the window of the map within
+    max_dist + 1 texels of the fragments' texels, runs the batched kernel
+    and copies the answers back, overlapping consecutive maps on its own
+    streams.  Answers are those of rbsm_batch_run on device copies."""
+
+    def __init__(self, max_fragments, max_width, max_height, slots=0, texture=True):
+        d = N.rbsm_stager_desc(int(max_fragments), int(max_width), int(max_height), int(slots),
+                               1 if texture else 0, 0)
+        h = ctypes.c_void_p(0)
+        N.check("rbsm_stager_create", N.lib().rbsm_stager_create(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+        self._inflight = []
+
+    def run(self, maps, jobs, max_dist=N.RBSM_MAXDIST_DEFAULT, tile_threads=0, ctas_per_sm=0, surrogate=None,
+            guard_tau=0.0, stream=None):
+        """Enqueue one host-resident batch on `stream` (the current torch
+        stream by default); the answers are in the jobs' host planes once
+        the stream has passed this point.  The tensors must stay alive until
+        then (the stager keeps references to the last two runs)."""
+        maps, jobs = list(maps), list(jobs)
+        md = (N.rbsm_map * len(maps))(*[_host_map_desc(m) for m in maps])
+        jd = (N.rbsm_job * len(jobs))(*[_host_job_desc(j) for j in jobs])
+        desc = N.rbsm_batch(md, len(maps), jd, len(jobs), _params(max_dist), int(tile_threads), int(ctas_per_sm),
+                            surrogate.state.data_ptr() if surrogate is not None else None, float(guard_tau))
+        N.check("rbsm_stager_run", N.lib().rbsm_stager_run(self.handle, ctypes.byref(desc), _stream_handle(stream)))
+        self._inflight = (self._inflight + [(maps, jobs)])[-2:]
+
+    def stats(self):
+        """(bytes copied in, bytes copied out) over every run so far (waits)."""
+        a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+        N.check("rbsm_stager_stats", N.lib().rbsm_stager_stats(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def status(self):
+        st = ctypes.c_int(0)
+        N.check("rbsm_stager_status", N.lib().rbsm_stager_status(self.handle, ctypes.byref(st)))
+        return st.value
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            N.check("rbsm_stager_destroy", N.lib().rbsm_stager_destroy(self.handle))
+        self.handle = None
+        self._inflight = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

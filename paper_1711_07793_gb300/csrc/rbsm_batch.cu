@@ -12,20 +12,11 @@
 #include "rbsm.h"
 #include "rbsm_device.cuh"
 #include "rbsm_batch_kernel.cuh"
+#include "rbsm_batch_host.h"
 #include "rbsm_host.h"
 #include "rbsm_mlp.cuh"
 
 namespace rbsm {
-
-// Launch shape of a batched launch: kernel variant, grid and dynamic shared
-// memory.  Kept apart from the launch itself so that it runs before any
-// stream capture (it sets a function attribute and queries occupancy).
-struct LaunchShape {
-    BatchKernelFn kernel;
-    int threads;
-    unsigned grid;
-    size_t smem;
-};
 
 // Per-kernel, per-device cache of "dynamic shared memory attribute set +
 // occupancy" (the attribute is a per-device property of each kernel).
@@ -149,8 +140,6 @@ int launch_kernel(const BatchArgs &args, const LaunchShape &sh, cudaStream_t str
     return RBSM_OK;
 }
 
-// Validate a batch and fill the kernel arguments (everything but the
-// workspace pointers).  Returns RBSM_OK or RBSM_ERR_ARG.
 int prepare_batch(const rbsm_batch *b, BatchArgs &a, int *threads)
 {
     if (!b || !b->maps || !b->jobs)

@@ -47,6 +47,8 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", offsetof(rbsm_job, frags), offsetof(rbsm_job, vis_silhouette),
          offsetof(rbsm_job, codes), offsetof(rbsm_batch, jobs), offsetof(rbsm_batch, params),
          offsetof(rbsm_batch, ctas_per_sm));
+  printf("%zu %zu %zu %zu\n", sizeof(rbsm_stager_desc), offsetof(rbsm_stager_desc, max_width),
+         offsetof(rbsm_stager_desc, slots), offsetof(rbsm_stager_desc, flags));
   return 0;
 }
 ''')
@@ -60,6 +62,9 @@ int main(void) {
                      ctypes.sizeof(N.rbsm_job), ctypes.sizeof(N.rbsm_batch)]
     assert offs == [N.rbsm_job.frags.offset, N.rbsm_job.vis_silhouette.offset, N.rbsm_job.codes.offset,
                     N.rbsm_batch.jobs.offset, N.rbsm_batch.params.offset, N.rbsm_batch.ctas_per_sm.offset]
+    st = [int(v) for v in lines[2].split()]
+    assert st == [ctypes.sizeof(N.rbsm_stager_desc), N.rbsm_stager_desc.max_width.offset,
+                  N.rbsm_stager_desc.slots.offset, N.rbsm_stager_desc.flags.offset]
 
 
 def test_bad_arguments_are_rejected_before_any_cuda_call(native):
@@ -100,6 +105,19 @@ def test_bad_arguments_are_rejected_before_any_cuda_call(native):
     assert lib.rbsm_batch_run(B(N.rbsm_batch(maps, 1, jobs, 0, p, 0, 0)), addr, 4096, None) == N.RBSM_ERR_ARG
     assert lib.rbsm_batch_run(B(N.rbsm_batch(maps, 1, jobs, 1, p, 192, 0)), addr, 4096, None) == N.RBSM_ERR_ARG
     assert lib.rbsm_batch_run(B(N.rbsm_batch(maps, 65, jobs, 1, p, 0, 0)), addr, 4096, None) == N.RBSM_ERR_ARG
+    # the stager: descriptors are checked before any CUDA call
+    h = ctypes.c_void_p(0)
+    for bad in (N.rbsm_stager_desc(0, 64, 64, 0, 0, 0), N.rbsm_stager_desc(10, 0, 64, 0, 0, 0),
+                N.rbsm_stager_desc(10, 64, 70000, 0, 0, 0), N.rbsm_stager_desc(10, 64, 64, 1, 0, 0),
+                N.rbsm_stager_desc(10, 64, 64, 5, 0, 0), N.rbsm_stager_desc(10, 64, 64, 0, 2, 0),
+                N.rbsm_stager_desc(10, 64, 64, 0, 0, 1)):
+        assert lib.rbsm_stager_create(B(bad), B(h)) == N.RBSM_ERR_ARG and not h.value
+    assert lib.rbsm_stager_create(None, B(h)) == N.RBSM_ERR_ARG
+    assert lib.rbsm_stager_run(None, B(batch), None) == N.RBSM_ERR_ARG
+    i64 = ctypes.c_int64(0)
+    assert lib.rbsm_stager_stats(None, B(i64), B(i64)) == N.RBSM_ERR_ARG
+    assert lib.rbsm_stager_status(None, B(ctypes.c_int(0))) == N.RBSM_ERR_ARG
+    assert lib.rbsm_stager_destroy(None) == N.RBSM_ERR_ARG
     assert lib.rbsm_status_string(N.RBSM_ERR_ARG) == b"invalid argument"
     assert lib.rbsm_version() >= 100
 
