@@ -291,15 +291,16 @@ int rbsm_batch_status(const void *workspace, int *status);
  * answers are those rbsm_batch_run gives on device copies of the whole
  * batch, bit for bit.  The window is the bounding box of the jobs' texels
  * (computed on the device from the staged fragments, with the texel
- * arithmetic of the kernels) grown by h and clipped to the map; the
- * texels outside it are never copied.
+ * arithmetic of the kernels) grown by h, its columns widened to multiples
+ * of 4 texels (16-byte row pieces) and clipped to the map; the texels
+ * outside it are never copied.
  *
  * Work per map, with no host wait anywhere: copies of the fragment planes
  * in, the texel bounds, a kernel that copies the window rows in from the
  * host map, the batched kernel, copies of the answers out.  These run on
  * the stager's own streams through a ring of device slots, so the copies
- * in of one map, the kernel of the previous one and the copies out of the
- * one before overlap.  The call is ordered after the work already enqueued
+ * in of one map, the window and kernel of the previous ones and the
+ * copies out of the one before overlap.  The call is ordered after the work already enqueued
  * on `stream`, and `stream` is ordered after the call's last copy out.
  *
  * desc: max_fragments = the largest sum of n over the jobs of one map;

@@ -2,8 +2,9 @@
 // of the map's jobs in, find the texel bounds of those fragments on the
 // device, copy in only the window of the map the path can read (the bounds
 // grown by max_dist + 1), run the batched kernel on the staged copies and
-// copy the answers out.  A ring of device slots and three streams (in,
-// kernel, out) let consecutive maps overlap; no step waits on the host.
+// copy the answers out.  A ring of device slots and four streams (in,
+// window, kernel, out) let consecutive maps overlap; no step waits on the
+// host.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -74,19 +75,22 @@ __global__ void __launch_bounds__(kBoundsThreads) texel_bounds(const float *__re
 
 // Copy the window of a host map (page-locked, read through its device
 // mapping) into the same texels of the slot's map: the texel bounds in win
-// grown by `halo` and clipped to the map.  One warp per row, four loads in
-// flight per lane.  Block 0 adds the window's bytes to *bytes_in.
+// grown by `halo`, clipped to the map and widened to columns 4k .. 4k+3
+// (also clipped), so that rows move in 16-byte pieces when both maps allow
+// it (`vec`: 16-byte aligned base and a pitch of a multiple of 4 floats on
+// both sides).  One warp per row.  Block 0 adds the window's bytes to
+// *bytes_in.
 __global__ void __launch_bounds__(kWindowThreads) stage_window(const float *__restrict__ src, long long src_pitch,
                                                                int width, int height, int halo,
                                                                float *__restrict__ dst, long long dst_pitch,
-                                                               const unsigned *win,
+                                                               int vec, const unsigned *win,
                                                                unsigned long long *bytes_in)
 {
     const unsigned hi_i = win[1], hi_j = win[3];
     if (hi_i == 0)
         return;
-    const int i0 = max((int)~win[0] - halo, 0);
-    const int i1 = min((int)(hi_i - 1u) + halo, width - 1);
+    const int i0 = max((int)~win[0] - halo, 0) & ~3;
+    const int i1 = min(min((int)(hi_i - 1u) + halo, width - 1) | 3, width - 1);
     const int j0 = max((int)~win[2] - halo, 0);
     const int j1 = min((int)(hi_j - 1u) + halo, height - 1);
     const int cols = i1 - i0 + 1, rows = j1 - j0 + 1;
@@ -95,15 +99,22 @@ __global__ void __launch_bounds__(kWindowThreads) stage_window(const float *__re
     for (int r = blockIdx.x * warps + (threadIdx.x >> 5); r < rows; r += gridDim.x * warps) {
         const float *s = src + (long long)(j0 + r) * src_pitch + i0;
         float *d = dst + (long long)(j0 + r) * dst_pitch + i0;
-        int c = lane;
-        for (; c + 96 < cols; c += 128) {
-            const float a = s[c], b = s[c + 32], e = s[c + 64], g = s[c + 96];
-            d[c] = a;
-            d[c + 32] = b;
-            d[c + 64] = e;
-            d[c + 96] = g;
+        int c = 0;
+        if (vec) {
+            const int n4 = cols >> 2;
+            const float4 *s4 = reinterpret_cast<const float4 *>(s);
+            float4 *d4 = reinterpret_cast<float4 *>(d);
+            int q = lane;
+            for (; q + 32 < n4; q += 64) {
+                const float4 a = s4[q], b = s4[q + 32];
+                d4[q] = a;
+                d4[q + 32] = b;
+            }
+            for (; q < n4; q += 32)
+                d4[q] = s4[q];
+            c = n4 << 2;
         }
-        for (; c < cols; c += 32)
+        for (c += lane; c < cols; c += 32)
             d[c] = s[c];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0)
@@ -124,7 +135,7 @@ struct Slot {
     uint64_t tex = 0;                 // texture of `map` for (tex_w, tex_h, tex_pitch)
     int tex_w = 0, tex_h = 0;
     long long tex_pitch = 0;
-    cudaEvent_t in_done = nullptr, cmp_done = nullptr, free_ = nullptr;
+    cudaEvent_t bounds_done = nullptr, in_done = nullptr, cmp_done = nullptr, free_ = nullptr;
     bool used = false;                // cmp_done / free_ recorded at least once
 };
 
@@ -154,7 +165,7 @@ struct rbsm_stager_s {
     long long map_pitch_align = 1;    // floats
     int sms = 1;
     rbsm::Slot slot[rbsm::kMaxSlots];
-    cudaStream_t s_in = nullptr, s_cmp = nullptr, s_out = nullptr;
+    cudaStream_t s_in = nullptr, s_win = nullptr, s_cmp = nullptr, s_out = nullptr;
     cudaEvent_t start = nullptr, end = nullptr;
     unsigned long long *window_bytes = nullptr;   // device counter
     long long host_bytes_in = 0, bytes_out = 0;
@@ -172,6 +183,8 @@ void release(rbsm_stager_s *st)
             rbsm_map_texture_destroy(s.tex);
         if (s.block)
             cudaFree(s.block);
+        if (s.bounds_done)
+            cudaEventDestroy(s.bounds_done);
         if (s.in_done)
             cudaEventDestroy(s.in_done);
         if (s.cmp_done)
@@ -181,7 +194,7 @@ void release(rbsm_stager_s *st)
     }
     if (st->window_bytes)
         cudaFree(st->window_bytes);
-    for (cudaStream_t s : {st->s_in, st->s_cmp, st->s_out})
+    for (cudaStream_t s : {st->s_in, st->s_win, st->s_cmp, st->s_out})
         if (s)
             cudaStreamDestroy(s);
     for (cudaEvent_t e : {st->start, st->end})
@@ -265,11 +278,16 @@ int run_map(rbsm_stager_s *st, const rbsm_batch *b, int map_index, const int *id
                                                                         hm.height, s.win);
         RBSM_CK(cudaGetLastError());
     }
-    stage_window<<<(unsigned)(2 * st->sms), kWindowThreads, 0, st->s_in>>>(
-        static_cast<const float *>(map_view), hm.pitch, hm.width, hm.height, max_dist + 1, s.map, pitch, s.win,
+    // the window copy runs on its own stream, beside the next map's
+    // fragment copies
+    RBSM_CK(cudaEventRecord(s.bounds_done, st->s_in));
+    RBSM_CK(cudaStreamWaitEvent(st->s_win, s.bounds_done, 0));
+    const int vec = (reinterpret_cast<uintptr_t>(map_view) & 15u) == 0 && hm.pitch % 4 == 0 && pitch % 4 == 0;
+    stage_window<<<(unsigned)(2 * st->sms), kWindowThreads, 0, st->s_win>>>(
+        static_cast<const float *>(map_view), hm.pitch, hm.width, hm.height, max_dist + 1, s.map, pitch, vec, s.win,
         st->window_bytes);
     RBSM_CK(cudaGetLastError());
-    RBSM_CK(cudaEventRecord(s.in_done, st->s_in));
+    RBSM_CK(cudaEventRecord(s.in_done, st->s_win));
 
     // kernel: the batch of this map's jobs on the staged copies
     uint64_t tex = 0;
@@ -397,7 +415,9 @@ int rbsm_stager_create(const rbsm_stager_desc *desc, rbsm_stager *out)
     if ((e = cudaDeviceGetAttribute(&pitch_align, cudaDevAttrTexturePitchAlignment, st->device)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&st->sms, cudaDevAttrMultiProcessorCount, st->device)) != cudaSuccess)
         return fail(e);
-    st->map_pitch_align = pitch_align > 4 ? pitch_align / 4 : 1;
+    // device map pitch: the texture pitch alignment, and at least 4 floats
+    // (16-byte rows for the window copy)
+    st->map_pitch_align = pitch_align > 16 ? pitch_align / 4 : 4;
     // plane capacity: max_fragments plus the alignment gap of every job
     st->plane_cap = (long long)align_up((size_t)desc->max_fragments, (size_t)kJobAlign) +
                     (long long)kJobAlign * RBSM_BATCH_MAX_JOBS;
@@ -425,7 +445,8 @@ int rbsm_stager_create(const rbsm_stager_desc *desc, rbsm_stager *out)
         s.win = reinterpret_cast<unsigned *>(p);
         p += align_up(4 * sizeof(unsigned), 256);
         s.ws = p;
-        if ((e = cudaEventCreateWithFlags(&s.in_done, cudaEventDisableTiming)) != cudaSuccess ||
+        if ((e = cudaEventCreateWithFlags(&s.bounds_done, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&s.in_done, cudaEventDisableTiming)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&s.cmp_done, cudaEventDisableTiming)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&s.free_, cudaEventDisableTiming)) != cudaSuccess)
             return fail(e);
@@ -436,6 +457,7 @@ int rbsm_stager_create(const rbsm_stager_desc *desc, rbsm_stager *out)
         (e = cudaMemset(st->window_bytes, 0, sizeof(unsigned long long))) != cudaSuccess)
         return fail(e);
     if ((e = cudaStreamCreateWithFlags(&st->s_in, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&st->s_win, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&st->s_cmp, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&st->s_out, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&st->start, cudaEventDisableTiming)) != cudaSuccess ||
@@ -487,7 +509,7 @@ int rbsm_stager_stats(rbsm_stager st, int64_t *bytes_in, int64_t *bytes_out)
     using namespace rbsm;
     if (!st || !bytes_in || !bytes_out)
         return RBSM_ERR_ARG;
-    for (cudaStream_t s : {st->s_in, st->s_cmp, st->s_out})
+    for (cudaStream_t s : {st->s_in, st->s_win, st->s_cmp, st->s_out})
         RBSM_CK(cudaStreamSynchronize(s));
     unsigned long long w = 0;
     RBSM_CK(cudaMemcpy(&w, st->window_bytes, sizeof w, cudaMemcpyDeviceToHost));
@@ -501,7 +523,7 @@ int rbsm_stager_status(rbsm_stager st, int *status)
     using namespace rbsm;
     if (!st || !status)
         return RBSM_ERR_ARG;
-    for (cudaStream_t s : {st->s_in, st->s_cmp, st->s_out})
+    for (cudaStream_t s : {st->s_in, st->s_win, st->s_cmp, st->s_out})
         RBSM_CK(cudaStreamSynchronize(s));
     *status = RBSM_OK;
     for (int k = 0; k < st->n_slots; ++k) {
@@ -519,7 +541,7 @@ int rbsm_stager_destroy(rbsm_stager st)
     if (!st)
         return RBSM_ERR_ARG;
     cudaError_t first = cudaSuccess;
-    for (cudaStream_t s : {st->s_in, st->s_cmp, st->s_out}) {
+    for (cudaStream_t s : {st->s_in, st->s_win, st->s_cmp, st->s_out}) {
         cudaError_t e = cudaStreamSynchronize(s);
         if (first == cudaSuccess)
             first = e;

@@ -49,9 +49,11 @@ def window_bytes(depth, xs, ys, max_dist):
     if i.size == 0:
         return 0
     halo = max_dist + 1
-    cols = min(i.max() + halo, w - 1) - max(i.min() - halo, 0) + 1
+    # columns widened to 4-texel boundaries (16-byte row pieces), clipped
+    i0 = max(i.min() - halo, 0) // 4 * 4
+    i1 = min(min(i.max() + halo, w - 1) | 3, w - 1)
     rows = min(j.max() + halo, h - 1) - max(j.min() - halo, 0) + 1
-    return int(rows * cols * 4)
+    return int(rows * (i1 - i0 + 1) * 4)
 
 
 def random_map(rng, w, h):
