@@ -29,6 +29,11 @@ def _load():
             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
             ctypes.c_int32, ctypes.c_int32,
             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.oracle_rpcf.restype = ctypes.c_int
+        lib.oracle_rpcf.argtypes = [
+            ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+            ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]
         lib.oracle_features.restype = ctypes.c_int
         lib.oracle_features.argtypes = [
             ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
@@ -72,6 +77,26 @@ def evaluate(depth, x, y, z, mode, max_dist=MAXDIST, want_rd=False, want_nrd=Fal
     if want_nrd:
         out["nrd"] = nrd
     return out
+
+
+def rpcf(depth, x, y, z, k=3, max_dist=MAXDIST):
+    """RPCF visibility (float64) of every fragment: the mean RSMSS answer of
+    the k x k samples shifted by whole texels around it (readings R18, R19
+    in rbsm_oracle.c; k = 1 is RSMSS)."""
+    lib = _load()
+    depth = np.ascontiguousarray(depth, dtype=np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    z = np.ascontiguousarray(z, dtype=np.float32)
+    n = x.shape[0]
+    if y.shape[0] != n or z.shape[0] != n:
+        raise ValueError("x, y, z must have the same length")
+    h, w = depth.shape
+    vis = np.empty(n, np.float64)
+    rc = lib.oracle_rpcf(_ptr(depth), w, h, w, _ptr(x), _ptr(y), _ptr(z), n, int(k), int(max_dist), _ptr(vis))
+    if rc != 0:
+        raise ValueError("oracle_rpcf rejected its arguments (rc=%d)" % rc)
+    return vis
 
 
 def features(depth, x, y, z):

@@ -214,12 +214,10 @@ static double filter_visibility(int dxq, int dyq, int dz, int cx, int cy, double
  * Code bits: 0-3 discontinuity directions (left, right, +y, -y), 4 = d.z
  * (shadow-test failed), 5-6 ends found along x (0..2), 7-8 ends found along
  * y, 9 = the fragment went through the edge traversal. */
-static void rbsm_fragment(const sm_t *sm, float x, float y, float pz, int mode, int max_dist,
-                          double *vis_out, uint16_t *code_out, int32_t rd_out[4], double nrd_out[4])
+static void rbsm_fragment_uv(const sm_t *sm, float u, float v, float pz, int mode, int max_dist,
+                             double *vis_out, uint16_t *code_out, int32_t rd_out[4], double nrd_out[4])
 {
-    /* R1, R17: texel and in-texel offset from the single-precision product */
-    float u = x * (float)sm->width;
-    float v = y * (float)sm->height;
+    /* R1, R17: texel and in-texel offset of the texel-space position (u, v) */
     float fu = floorf(u), fv = floorf(v);
     float fx = u - fu, fy = v - fv;
     /* clamp while still a float (fmaxf/fminf pick the non-NaN operand, so a
@@ -278,6 +276,15 @@ static void rbsm_fragment(const sm_t *sm, float x, float y, float pz, int mode, 
         for (int k = 0; k < 4; ++k) nrd_out[k] = nrd[k];
 }
 
+/* R1: the texel-space position is the single-precision product x * W. */
+static void rbsm_fragment(const sm_t *sm, float x, float y, float pz, int mode, int max_dist,
+                          double *vis_out, uint16_t *code_out, int32_t rd_out[4], double nrd_out[4])
+{
+    float u = x * (float)sm->width;
+    float v = y * (float)sm->height;
+    rbsm_fragment_uv(sm, u, v, pz, mode, max_dist, vis_out, code_out, rd_out, nrd_out);
+}
+
 /* Evaluate n fragments.  Returns 0, or -1 on invalid arguments.
  * rd (n*4 int32), nrd (n*4 double) and codes may be NULL. */
 int oracle_rbsm_eval(const float *depth, int32_t width, int32_t height, int64_t pitch,
@@ -297,6 +304,48 @@ int oracle_rbsm_eval(const float *depth, int32_t width, int32_t height, int64_t 
                       codes ? &codes[t] : NULL,
                       rd ? &rd[4 * t] : NULL,
                       nrd ? &nrd[4 * t] : NULL);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * RPCF: percentage-closer filtering over the RSMSS answer (§5.3 suppresses
+ * the skeleton artifacts of the filtered edges with PCF; the paper prints no
+ * kernel for it).  Readings:
+ *   R18 the k x k PCF samples are the fragment's texel-space position
+ *       (u, v) = (x W, y H) (single precision, R1) shifted by whole texels,
+ *       (u + a, v + b) for a, b = -(k-1)/2 .. (k-1)/2, each shift a
+ *       single-precision add; every sample keeps the fragment's depth.
+ *   R19 a sample's answer is the Listing 5 (RSMSS) visibility of that
+ *       position, walks and all; the RPCF answer is their mean, summed with
+ *       b outer and a inner.
+ * k = 1 is RSMSS itself.  Returns 0, or -1 on invalid arguments (k must be
+ * odd, 1..7). */
+int oracle_rpcf(const float *depth, int32_t width, int32_t height, int64_t pitch,
+                const float *px, const float *py, const float *pz, int64_t n,
+                int32_t k, int32_t max_dist, double *vis)
+{
+    if (!depth || width < 1 || height < 1 || pitch < width || n < 0 || max_dist < 1)
+        return -1;
+    if (k < 1 || k > 7 || (k & 1) == 0)
+        return -1;
+    if (n > 0 && (!px || !py || !pz || !vis))
+        return -1;
+    sm_t sm = {depth, width, height, pitch};
+    const int r = (k - 1) / 2;
+    for (int64_t t = 0; t < n; ++t) {
+        float u = px[t] * (float)width;
+        float v = py[t] * (float)height;
+        double sum = 0.0;
+        for (int b = -r; b <= r; ++b) {
+            for (int a = -r; a <= r; ++a) {
+                double va;
+                rbsm_fragment_uv(&sm, u + (float)a, v + (float)b, pz[t], ORACLE_MODE_FILTER, max_dist, &va,
+                                 NULL, NULL, NULL);
+                sum += va;
+            }
+        }
+        vis[t] = sum / (double)(k * k);
     }
     return 0;
 }
