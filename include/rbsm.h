@@ -140,6 +140,21 @@ int rsmss_filter(const rbsm_map *map, const rbsm_frags *frags, float *vis,
                  uint16_t *codes, const rbsm_params *params, void *stream);
 
 /*
+ * RPCF: percentage-closer filtering over the RSMSS answer (§5.3: the
+ * skeleton artifacts along filtered edges are suppressed with PCF; the
+ * paper prints no kernel for it).  For every fragment: the mean of the
+ * Listing 5 (RSMSS) answers of the k x k samples at its texel-space
+ * position (x W, y H), shifted by whole texels (u + a, v + b) for a, b in
+ * -(k-1)/2 .. (k-1)/2 (float32 adds), each with the fragment's depth,
+ * summed with b outer and a inner.  k = 1 is rsmss_filter itself.
+ *   k: odd, 1..RBSM_RPCF_MAX_K.  vis: output, n floats in [0, 1].
+ * Errors as for rsmss_filter, and RBSM_ERR_ARG for an even or out-of-range k.
+ */
+#define RBSM_RPCF_MAX_K 7
+int rbsm_rpcf(const rbsm_map *map, const rbsm_frags *frags, float *vis, int32_t k,
+              const rbsm_params *params, void *stream);
+
+/*
  * Batched evaluation: many shadow maps (lights, cascades) against many
  * fragment sets (views) in ONE persistent kernel launch.  Not in the paper,
  * which evaluates one map per shader pass; every job's answers are

@@ -24,6 +24,7 @@ RBSM_MODE_BOTH = 3
 RBSM_MAXDIST_DEFAULT = 16
 RBSM_BATCH_MAX_MAPS = 64
 RBSM_BATCH_MAX_JOBS = 256
+RBSM_RPCF_MAX_K = 7
 
 
 class rbsm_map(ctypes.Structure):
@@ -93,6 +94,8 @@ def _declare(lib):
         f = getattr(lib, name)
         f.restype = i32
         f.argtypes = [_P(rbsm_map), _P(rbsm_frags), vp, vp, _P(rbsm_params), vp]
+    lib.rbsm_rpcf.restype = i32
+    lib.rbsm_rpcf.argtypes = [_P(rbsm_map), _P(rbsm_frags), vp, ctypes.c_int32, _P(rbsm_params), vp]
     lib.rbsm_map_texture_create.restype = i32
     lib.rbsm_map_texture_create.argtypes = [_P(rbsm_map), _P(ctypes.c_uint64)]
     lib.rbsm_map_texture_destroy.restype = i32

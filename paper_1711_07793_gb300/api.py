@@ -139,6 +139,21 @@ def rsmss_filter(depth, x, y, z, vis=None, codes=False, max_dist=N.RBSM_MAXDIST_
     """Revectorization-based shadow filtering (Listing 5): returns (vis, codes or None)."""
     return _single(N.lib().rsmss_filter, "rsmss_filter", depth, x, y, z, vis, codes, max_dist, stream)
 
+def rbsm_rpcf(depth, x, y, z, k=3, vis=None, max_dist=N.RBSM_MAXDIST_DEFAULT, stream=None):
+    """RPCF (rbsm_rpcf): the mean RSMSS answer of the k x k samples shifted
+    by whole texels around each fragment (PCF over Listing 5, §5.3).
+    CUDA tensors (or a MapTexture); returns vis."""
+    m = map_desc(depth)
+    f = frags_desc(x, y, z)
+    if vis is None:
+        vis = torch.empty(f.n, dtype=torch.float32, device=x.device)
+    else:
+        _check_plane("vis", vis, f.n)
+    p = _params(max_dist)
+    N.check("rbsm_rpcf", N.lib().rbsm_rpcf(ctypes.byref(m), ctypes.byref(f), ctypes.c_void_p(vis.data_ptr()),
+                                           int(k), ctypes.byref(p), _stream_handle(stream)))
+    return vis
+
 
 class Job:
     """One fragment set against one map of a batch.  Outputs are allocated

@@ -43,15 +43,20 @@ __device__ __forceinline__ int shadow_test(float pz, float zt)
     return pz > zt ? 0 : 1;
 }
 
-// Texel coordinate and in-texel offset along one axis, float32 as the
-// paper's GLSL: u = x * size, t = clamp(floor(u)), f = u - floor(u).
-__device__ __forceinline__ void texel_coord(float x, int size, int &t, float &f)
+// Texel and in-texel offset of a texel-space position u along one axis:
+// t = clamp(floor(u)), f = u - floor(u) (float32, as the paper's GLSL).
+__device__ __forceinline__ void texel_of(float u, int size, int &t, float &f)
 {
-    float u = __fmul_rn(x, (float)size);
     float fu = floorf(u);
     f = __fsub_rn(u, fu);
     float c = fminf(fmaxf(fu, 0.0f), (float)(size - 1));
     t = (int)c;
+}
+
+// The same from a texture coordinate: u = x * size.
+__device__ __forceinline__ void texel_coord(float x, int size, int &t, float &f)
+{
+    texel_of(__fmul_rn(x, (float)size), size, t, f);
 }
 
 // Listing 3 along one axis, both directions.  A texel of the walk continues
@@ -262,8 +267,8 @@ __device__ __forceinline__ bool classify_from(float pz, float zc, float zl, floa
 // fragment (and of the other fragments of the lane) can all be in flight at
 // once.
 template <int MODE, bool CODES>
-__device__ __forceinline__ bool classify(const MapDev &m, float x, float y, float pz,
-                                         FragResult &r, uint32_t &bits)
+__device__ __forceinline__ bool classify_uv(const MapDev &m, float u, float v, float pz,
+                                            FragResult &r, uint32_t &bits)
 {
     if (m.tex) {
         // Texel coordinates in float (clamp(floor(u)) is an integer-valued
@@ -273,16 +278,16 @@ __device__ __forceinline__ bool classify(const MapDev &m, float x, float y, floa
         // i-1..i, rows j-1..j; at (i+1, j+1) columns i..i+1, rows j..j+1.
         // Gather order: x = (lo col, hi row), y = (hi, hi), z = (hi, lo),
         // w = (lo, lo).
-        const float ci = fminf(fmaxf(floorf(__fmul_rn(x, (float)m.width)), 0.0f), (float)(m.width - 1));
-        const float cj = fminf(fmaxf(floorf(__fmul_rn(y, (float)m.height)), 0.0f), (float)(m.height - 1));
+        const float ci = fminf(fmaxf(floorf(u), 0.0f), (float)(m.width - 1));
+        const float cj = fminf(fmaxf(floorf(v), 0.0f), (float)(m.height - 1));
         const float4 a = tex2Dgather<float4>(m.tex, ci, cj, 0);
         const float4 b = tex2Dgather<float4>(m.tex, ci + 1.0f, cj + 1.0f, 0);
         return classify_from<MODE, CODES>(pz, a.y, a.x, b.z, b.x, a.z, r, bits);
     }
     int i, j;
     float fx, fy;
-    texel_coord(x, m.width, i, fx);
-    texel_coord(y, m.height, j, fy);
+    texel_of(u, m.width, i, fx);
+    texel_of(v, m.height, j, fy);
     const float *c = m.depth + (long long)j * m.pitch + i;
     const float zc = __ldg(c);
     const int s0 = shadow_test(pz, zc);
@@ -318,15 +323,24 @@ __device__ __forceinline__ bool classify(const MapDev &m, float x, float y, floa
     return edge;
 }
 
-// Steps 3-4 for one edge fragment (recomputes its texel from x, y).
+// Steps 1-2 from a texture coordinate (u = x * W, v = y * H in float32).
+template <int MODE, bool CODES>
+__device__ __forceinline__ bool classify(const MapDev &m, float x, float y, float pz,
+                                         FragResult &r, uint32_t &bits)
+{
+    return classify_uv<MODE, CODES>(m, __fmul_rn(x, (float)m.width), __fmul_rn(y, (float)m.height), pz, r, bits);
+}
+
+// Steps 3-4 for one edge fragment at texel-space position (u, v)
+// (recomputes its texel).
 template <int MODE>
-__device__ __forceinline__ void resolve_edge(const MapDev &m, float x, float y, float pz,
-                                             uint32_t bits, int max_dist, FragResult &r)
+__device__ __forceinline__ void resolve_edge_uv(const MapDev &m, float u, float v, float pz,
+                                                uint32_t bits, int max_dist, FragResult &r)
 {
     int i, j;
     float fx, fy;
-    texel_coord(x, m.width, i, fx);
-    texel_coord(y, m.height, j, fy);
+    texel_of(u, m.width, i, fx);
+    texel_of(v, m.height, j, fy);
     int s0 = bits & 1;
     bool dl = (bits >> 1) & 1, dr = (bits >> 2) & 1, du = (bits >> 3) & 1, dd = (bits >> 4) & 1;
     // computeFragmentDistanceToSE: the four walks -x, +x, -y, +y
@@ -345,6 +359,14 @@ __device__ __forceinline__ void resolve_edge(const MapDev &m, float x, float y, 
         r.sil = s0 ? silhouette(dx3, dy3, ex, ey, nx, ny) : 0.0f;
     if (MODE & 2)
         r.fil = filter(dx3, dy3, 1 - s0, ex, ey, nx, ny);
+}
+
+// Steps 3-4 from a texture coordinate.
+template <int MODE>
+__device__ __forceinline__ void resolve_edge(const MapDev &m, float x, float y, float pz,
+                                             uint32_t bits, int max_dist, FragResult &r)
+{
+    resolve_edge_uv<MODE>(m, __fmul_rn(x, (float)m.width), __fmul_rn(y, (float)m.height), pz, bits, max_dist, r);
 }
 
 // ------------------------------------------------------------ warp tiles --

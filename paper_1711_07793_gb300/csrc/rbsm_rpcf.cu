@@ -1,0 +1,245 @@
+// RPCF: percentage-closer filtering over the RSMSS answer (§5.3 removes the
+// skeleton artifacts of the filtered edges with PCF; the paper prints no
+// kernel).  A fragment's answer is the mean Listing 5 answer of the k x k
+// samples at its texel-space position shifted by whole texels, (u + a,
+// v + b), each with the fragment's depth.
+//
+// Same warp-tile scheme as the other kernels, with the sample as the unit
+// of deferred work: a lane classifies its fragments' samples (two texture
+// gathers or five loads each); off-edge samples add their shadow test at
+// once, edge samples go to the warp's queue (fragment and sample index; the
+// drain classifies the sample again) and are walked 32 at a time on full
+// warps.  For k > 1 the per-fragment sum is kept in the output plane as
+// a fixed-point integer with 25 fraction bits (each sample answer rounded to
+// 2^-25, at most 49 * 2^25 < 2^31 in total), so the adds of the deferred
+// samples commute and the result does not depend on their order; a second
+// pass turns the sum into the mean (bit 31 marks a NaN sample answer).
+// For k = 1 there is nothing to add and the answers are stored as floats
+// (rsmss_filter's bits).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "rbsm.h"
+#include "rbsm_device.cuh"
+#include "rbsm_host.h"
+
+namespace rbsm {
+namespace {
+
+constexpr int kRpcfThreads = 256;
+constexpr float kFix = 33554432.0f;            // 2^25
+constexpr float kUnfix = 1.0f / 33554432.0f;   // 2^-25 (exact)
+constexpr uint32_t kNanFlag = 0x80000000u;     // above any sum (49 * 2^25 < 2^31): the mean is NaN
+constexpr int kRpcfQueueCap = 64;              // < 32 left over + one sample of every lane
+
+struct RpcfQueue {
+    EdgeEntry q[kRpcfQueueCap];
+};
+
+__device__ __forceinline__ uint32_t to_fix(float v)
+{
+    return (uint32_t)__float2uint_rn(__fmul_rn(v, kFix));
+}
+
+template <int K, int kThreads>
+__global__ void __launch_bounds__(kThreads, 1024 / kThreads)
+rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict__ y,
+            const float *__restrict__ z, long long n, float *__restrict__ vis, int max_dist, bool vec_planes)
+{
+    constexpr int kWarps = kThreads / 32;
+    constexpr int R = (K - 1) / 2;
+    __shared__ RpcfQueue wq[kWarps];
+    const unsigned lane = lane_id();
+    const unsigned below = (1u << lane) - 1u;
+    const int warp = threadIdx.x >> 5;
+    const long long stride = (long long)gridDim.x * kWarps;
+    const long long tiles = (n + kWarpTile - 1) / kWarpTile;
+    long long tile = (long long)blockIdx.x * kWarps + warp;
+    if (tile >= tiles)
+        return;
+    const float W = (float)m.width, H = (float)m.height;
+    uint32_t *acc = reinterpret_cast<uint32_t *>(vis);
+    auto io_of = [&](long long tl) {
+        WarpTileIO t;
+        t.x = x; t.y = y; t.z = z; t.sil = nullptr; t.fil = vis; t.codes = nullptr;
+        t.first = tl * kWarpTile;
+        const long long left = n - t.first;
+        t.count = left < kWarpTile ? (int)left : kWarpTile;
+        t.job = 0;
+        t.vec = vec_planes && t.count == kWarpTile;
+        return t;
+    };
+    // drain rounds of 32 queued edge samples: walk, answer, add
+    auto drain = [&](int &queued, bool all) {
+        while (queued >= 32 || (all && queued > 0)) {
+            __syncwarp();                  // entries and the fragments' base values are visible
+            const int base = queued >= 32 ? queued - 32 : 0;
+            const int q = base + (int)lane;
+            if (q < queued) {
+                const EdgeEntry e = wq[warp].q[q];
+                const uint32_t i = e.idx;
+                const int sample = (int)e.bits_job;
+                const float ua = __fadd_rn(__fmul_rn(__ldg(x + i), W), (float)(sample % K - R));
+                const float vb = __fadd_rn(__fmul_rn(__ldg(y + i), H), (float)(sample / K - R));
+                const float pz = __ldg(z + i);
+                FragResult r;
+                uint32_t bits;
+                classify_uv<2, false>(m, ua, vb, pz, r, bits);    // the sample's discontinuity again
+                resolve_edge_uv<2>(m, ua, vb, pz, bits, max_dist, r);
+                if (K == 1)
+                    vis[i] = r.fil;
+                else if (r.fil != r.fil)
+                    atomicOr(acc + i, kNanFlag);      // a NaN answer (NaN or infinite coordinates)
+                else
+                    atomicAdd(acc + i, to_fix(r.fil));
+            }
+            __syncwarp();                  // entries read before they are overwritten
+            queued = base;
+        }
+    };
+    WarpTileIO t = io_of(tile);
+    LaneCoords c;
+    load_tile(t, lane, c);
+    int queued = 0;
+    for (;;) {
+        const long long nt = tile + stride;
+        const bool more = nt < tiles;
+        WarpTileIO tn;
+        LaneCoords cn;
+        if (more) {
+            tn = io_of(nt);
+            load_tile(tn, lane, cn);       // next tile's loads fly during this tile
+        }
+#pragma unroll 1
+        for (int e = 0; e < kPerThread; ++e) {
+            const int s = t.vec ? (int)(kPerThread * lane) + e : (int)lane + 32 * e;
+            const bool valid = s < t.count;
+            const float xe = e == 0 ? c.x[0] : e == 1 ? c.x[1] : e == 2 ? c.x[2] : c.x[3];
+            const float ye = e == 0 ? c.y[0] : e == 1 ? c.y[1] : e == 2 ? c.y[2] : c.y[3];
+            const float ze = e == 0 ? c.z[0] : e == 1 ? c.z[1] : e == 2 ? c.z[2] : c.z[3];
+            const float u = __fmul_rn(xe, W), v = __fmul_rn(ye, H);
+            // all samples' texel reads first; off-edge samples add their
+            // shadow test to the base value, edge samples set their bit
+            uint64_t edges = 0;
+            uint32_t base = 0;
+            float single = 0.0f;
+#pragma unroll
+            for (int q = 0; q < K * K; ++q) {
+                FragResult r{0.0f, 0.0f, 0};
+                uint32_t bits = 0;
+                const bool edge = valid && classify_uv<2, false>(m, __fadd_rn(u, (float)(q % K - R)),
+                                                                 __fadd_rn(v, (float)(q / K - R)), ze, r, bits);
+                if (edge) {
+                    edges |= 1ull << q;
+                } else {
+                    base += r.fil != 0.0f ? (1u << 25) : 0u;
+                    single = r.fil;
+                }
+            }
+            // the base value is stored before any deferred sample of this
+            // fragment can add to it ...
+            if (valid) {
+                if (K == 1)
+                    vis[t.first + s] = single;
+                else
+                    acc[t.first + s] = base;
+            }
+            // ... then the edge samples are queued, one sample index at a
+            // time, and walked whenever 32 are waiting
+            if (__any_sync(0xffffffffu, edges != 0)) {
+#pragma unroll 1
+                for (int q = 0; q < K * K; ++q) {
+                    const bool eq = (edges >> q) & 1ull;
+                    const unsigned mask = __ballot_sync(0xffffffffu, eq);
+                    if (eq)
+                        wq[warp].q[queued + __popc(mask & below)] = EdgeEntry{(uint32_t)(t.first + s), (uint32_t)q};
+                    queued += __popc(mask);
+                    drain(queued, false);
+                }
+            }
+        }
+        if (!more)
+            break;
+        tile = nt;
+        t = tn;
+        c = cn;
+    }
+    drain(queued, true);
+}
+
+// The mean from the fixed-point sum: (sum * 2^-25) / k^2, or NaN when a
+// sample's answer was NaN (as a float sum would carry it).
+template <int K>
+__global__ void __launch_bounds__(256) rpcf_finish(float *__restrict__ vis, long long n)
+{
+    uint32_t *acc = reinterpret_cast<uint32_t *>(vis);
+    const float count = (float)(K * K);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t a = acc[i];
+        vis[i] = (a & kNanFlag) ? __int_as_float(0x7fc00000)
+                                : __fdiv_rn(__fmul_rn(__uint2float_rn(a), kUnfix), count);
+    }
+}
+
+template <int K>
+int launch_rpcf(const rbsm_map &map, const rbsm_frags &f, float *vis, int max_dist, cudaStream_t stream)
+{
+    auto kern = rpcf_kernel<K, kRpcfThreads>;
+    static KernelSetup setup;
+    int occupancy = 0;
+    int rc = setup.get(kern, kRpcfThreads, 0, &occupancy);
+    if (rc != RBSM_OK)
+        return rc;
+    const int sms = device_sm_count();
+    if (sms <= 0)
+        return cuda_fail(cudaErrorNoDevice);
+    const long long warp_tiles = (f.n + kWarpTile - 1) / kWarpTile;
+    const long long blocks_needed = (warp_tiles + kRpcfThreads / 32 - 1) / (kRpcfThreads / 32);
+    long long grid = (long long)sms * occupancy;
+    if (grid > blocks_needed)
+        grid = blocks_needed;
+    const bool vec = aligned16(f.x) && aligned16(f.y) && aligned16(f.z);
+    kern<<<(unsigned)grid, kRpcfThreads, 0, stream>>>(to_dev(map), f.x, f.y, f.z, f.n, vis, max_dist, vec);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    if (K > 1) {
+        long long blocks = (f.n + 255) / 256;
+        if (blocks > 8LL * sms)
+            blocks = 8LL * sms;
+        rpcf_finish<K><<<(unsigned)blocks, 256, 0, stream>>>(vis, f.n);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return cuda_fail(e);
+    }
+    return RBSM_OK;
+}
+
+}  // namespace
+}  // namespace rbsm
+
+extern "C" int rbsm_rpcf(const rbsm_map *map, const rbsm_frags *frags, float *vis, int32_t k,
+                         const rbsm_params *params, void *stream)
+{
+    using namespace rbsm;
+    int rc, max_dist;
+    if ((rc = check_map(map)) != RBSM_OK) return rc;
+    if ((rc = check_frags(frags)) != RBSM_OK) return rc;
+    if ((rc = check_params(params, &max_dist)) != RBSM_OK) return rc;
+    if (k < 1 || k > RBSM_RPCF_MAX_K || (k & 1) == 0)
+        return RBSM_ERR_ARG;
+    if (frags->n > 0 && !vis)
+        return RBSM_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(vis) & 3u) != 0)
+        return RBSM_ERR_ARG;
+    if (frags->n == 0)
+        return RBSM_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    switch (k) {
+    case 1: return launch_rpcf<1>(*map, *frags, vis, max_dist, s);
+    case 3: return launch_rpcf<3>(*map, *frags, vis, max_dist, s);
+    case 5: return launch_rpcf<5>(*map, *frags, vis, max_dist, s);
+    default: return launch_rpcf<7>(*map, *frags, vis, max_dist, s);
+    }
+}

@@ -91,6 +91,12 @@ def test_bad_arguments_are_rejected_before_any_cuda_call(native):
         assert fn(B(good_map), B(good_frags), addr, None, B(N.rbsm_params(16, 1)), None) == N.RBSM_ERR_ARG
         # n == 0 enqueues nothing and succeeds without touching the device
         assert fn(B(good_map), B(N.rbsm_frags(None, None, None, 0)), None, None, None, None) == N.RBSM_OK
+    for k in (0, 2, 9, -3):
+        assert lib.rbsm_rpcf(B(good_map), B(good_frags), addr, k, B(p), None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_rpcf(None, B(good_frags), addr, 3, B(p), None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_rpcf(B(good_map), B(good_frags), None, 3, B(p), None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_rpcf(B(good_map), B(good_frags), addr + 2, 3, B(p), None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_rpcf(B(good_map), B(N.rbsm_frags(None, None, None, 0)), None, 3, None, None) == N.RBSM_OK
     maps = (N.rbsm_map * 1)(good_map)
     jobs = (N.rbsm_job * 1)(N.rbsm_job(0, 3, good_frags, addr, addr, None))
     batch = N.rbsm_batch(maps, 1, jobs, 1, p, 0, 0)

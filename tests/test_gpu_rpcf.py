@@ -1,0 +1,138 @@
+"""GPU parity of RPCF (rbsm_rpcf, PCF over the RSMSS answer, §5.3) with the
+oracle: every fragment within 1e-5 (the oracle sums float64 answers, the
+kernel float32 ones in the same order); k = 1 equals rsmss_filter bit for
+bit; plain loads and texture gathers give the same bits."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import rbsm as orc  # noqa: E402
+from tests import shapes  # noqa: E402
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1711_07793_gb300 import api as A
+    return A
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def gpu_rpcf(api, depth, x, y, z, k, max_dist=16, texture=False):
+    from paper_1711_07793_gb300 import _native as N
+    d = dev(depth) if isinstance(depth, np.ndarray) else depth
+    tex = None
+    if texture:
+        try:
+            tex = api.MapTexture(d)
+        except N.RBSMError as e:
+            assert e.code == N.RBSM_ERR_ARG
+            return None
+    v = api.rbsm_rpcf(tex or d, dev(x), dev(y), dev(z), k=k, max_dist=max_dist)
+    torch.cuda.synchronize()
+    out = v.cpu().numpy()
+    if tex is not None:
+        tex.close()
+    return out
+
+
+def check(api, depth, x, y, z, k, where, max_dist=16):
+    ref = orc.rpcf(depth, x, y, z, k=k, max_dist=max_dist)
+    got = gpu_rpcf(api, depth, x, y, z, k, max_dist)
+    g = got.astype(np.float64)
+    both_nan = np.isnan(g) & np.isnan(ref)
+    assert not np.any(np.isnan(g) ^ np.isnan(ref)), where
+    diff = np.abs(g - ref)
+    diff[both_nan] = 0.0
+    assert diff.max(initial=0.0) <= TOL, "%s: max |diff| %g" % (where, diff.max())
+    tex = gpu_rpcf(api, depth, x, y, z, k, max_dist, texture=True)
+    if tex is not None:
+        assert np.array_equal(tex.view(np.uint32), got.view(np.uint32)), where + " texture"
+    return got
+
+
+@pytest.mark.parametrize("k", [1, 3, 5, 7])
+def test_config1(api, k):
+    import rbsm_scenes as sc
+    f = sc.config1(0)
+    got = check(api, f.depth, f.x, f.y, f.z, k, "C1 k=%d" % k)
+    if k == 1:
+        vis, _ = api.rsmss_filter(dev(f.depth), dev(f.x), dev(f.y), dev(f.z))
+        assert np.array_equal(vis.cpu().numpy().view(np.uint32), got.view(np.uint32))
+
+
+def test_config2_sampled(api):
+    import rbsm_scenes as sc
+    f = sc.config2(0, screen=(960, 540))
+    check(api, f.depth, f.x, f.y, f.z, 3, "C2")
+
+
+@pytest.mark.parametrize("n", [1, 3, 127, 129, 4097])
+def test_ragged(api, n):
+    rng = np.random.default_rng(n)
+    depth = np.where(rng.random((40, 56)) < 0.3, np.float32(0.5), np.float32(1.0)).astype(np.float32)
+    x = rng.uniform(0, 1, n).astype(np.float32)
+    y = rng.uniform(0, 1, n).astype(np.float32)
+    check(api, depth, x, y, np.ones_like(x), 3, "n=%d" % n)
+
+
+def test_empty(api):
+    v = api.rbsm_rpcf(dev(np.ones((4, 4), np.float32)), *(torch.empty(0, device="cuda") for _ in range(3)))
+    assert v.shape == (0,)
+
+
+@pytest.mark.parametrize("w,h", [(1, 1), (2, 2), (1, 9), (9, 1), (3, 700), (257, 129)])
+def test_odd_maps_and_borders(api, w, h):
+    rng = np.random.default_rng(w * 1000 + h)
+    depth = np.where(rng.random((h, w)) < 0.35, np.float32(0.25), np.float32(1.0)).astype(np.float32)
+    x = rng.uniform(-0.3, 1.3, 6000).astype(np.float32)
+    y = rng.uniform(-0.3, 1.3, 6000).astype(np.float32)
+    x[::71] = np.nan
+    y[::67] = np.inf
+    check(api, depth, x, y, np.full_like(x, 0.5), 3, "%dx%d" % (w, h))
+
+
+@pytest.mark.parametrize("max_dist", [1, 2, 16, 255])
+def test_max_dist_and_staircases(api, max_dist):
+    for run_len in (1, 3, 16):
+        mask = shapes.staircase_mask(96, run_len, 4, 30)
+        depth = np.where(mask, shapes.BLOCKER, shapes.LIT).astype(np.float32)
+        X, Y = shapes.fragment_grid(10, 86, 10, 86, [(0.25, 0.25), (0.75, 0.6)])
+        x, y = shapes.to_texcoords(X, Y, 96, 96)
+        for k in (3, 5):
+            check(api, depth, x, y, np.ones_like(x), k, "stair %d md %d k %d" % (run_len, max_dist, k), max_dist)
+
+
+def test_rejects_bad_k(api):
+    from paper_1711_07793_gb300 import _native as N
+    d, x = dev(np.ones((4, 4), np.float32)), torch.zeros(8, device="cuda")
+    for k in (0, 2, 9):
+        with pytest.raises(N.RBSMError) as e:
+            api.rbsm_rpcf(d, x, x, x, k=k)
+        assert e.value.code == N.RBSM_ERR_ARG
+
+
+def test_full_size_frame_sampled(api):
+    """One 3840x2160 frame on an 8192^2 map at the bench's size: every
+    answer of a sample of fragments against the oracle."""
+    import bench
+    _, host = bench.make_workload(1, 0, pin=False)
+    depth = host[0]["depth"].numpy()
+    x, y, z = (host[0]["xyz"][q].numpy() for q in range(3))
+    got = gpu_rpcf(api, depth, x, y, z, 3)
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(x.shape[0], 200000, replace=False))
+    ref = orc.rpcf(depth, x[idx], y[idx], z[idx], k=3)
+    assert np.abs(got[idx].astype(np.float64) - ref).max() <= TOL
+    assert 0.0 < np.mean((ref > 0) & (ref < 1)) < 0.5
