@@ -53,6 +53,7 @@ def parse_args(argv=None):
     p.add_argument("--skip-e2e", action="store_true", help="profiling runs only")
     p.add_argument("--skip-cpu", action="store_true", help="profiling runs only")
     p.add_argument("--skip-learned", action="store_true", help="profiling runs only")
+    p.add_argument("--skip-rpcf", action="store_true", help="profiling runs only")
     p.add_argument("--guard-tau", type=float, default=0.05, help="surrogate guard (largest accepted error estimate)")
     p.add_argument("--texture", choices=["on", "off"], default="on",
                    help="read each map's four-neighbourhood with texture gathers (rbsm_map_texture_create)")
@@ -380,6 +381,10 @@ def run_ours(args, rank, world, local_rank):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
                "path": "rbsm_stager_run: pinned host maps/fragments/answers; fragment planes and map windows in"}
 
+    rpcf = None
+    if not args.skip_rpcf:
+        rpcf = measure_rpcf(api, texs or maps, xyz, frames, n_frag, args, stream)
+
     learned = None
     if not args.skip_learned:
         learned = compare_learned(api, texs or maps, xyz, frames, n_frag, args, stream)
@@ -412,6 +417,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": e2e,
         "cpu_baseline": cpu,
         "learned": learned,
+        "rpcf": rpcf,
         "gpu_launches": args.steps,
         "clocks": clocks,
         "edge": {"unique_texels_per_frame": statistics.mean(h["U"] for h in host)},
@@ -485,6 +491,44 @@ def compare_learned(api, maps, xyz, frames, n_frag, args, stream):
             "error_vs_plain_answered": {"mean": float(dn.mean()) if dn.numel() else None, "p99": q(dn, 0.99),
                                         "max": float(dn.max()) if dn.numel() else None},
             "checkpoint": {k: net.header.get(k) for k in ("samples", "epochs", "data", "loss_per_epoch")}}
+
+
+def measure_rpcf(api, maps, xyz, frames, n_frag, args, stream, k=3):
+    """RPCF (PCF over the RSMSS answer, rbsm_rpcf) on the same frames, one
+    launch per frame: time per 32-frame step next to rsmss_filter's, and
+    the algorithmic-byte rate of its launches (the same bytes per fragment
+    as RSMSS: the k x k samples re-read texels that are already on chip)."""
+    import torch
+    outs = [torch.empty(n_frag, dtype=torch.float32, device=xyz[0].device) for _ in range(frames)]
+    steps = max(3, min(args.steps // 20, 20))
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def rpcf():
+        for f in range(frames):
+            api.rbsm_rpcf(maps[f], xyz[f][0], xyz[f][1], xyz[f][2], k=k, vis=outs[f])
+
+    def rsmss():
+        for f in range(frames):
+            api.rsmss_filter(maps[f], xyz[f][0], xyz[f][1], xyz[f][2], vis=outs[f])
+
+    ms = timed(rpcf)
+    ms_rsmss = timed(rsmss)
+    fps = lambda t: frames * n_frag / (t * 1e-3) / 1e9
+    return {"metric": "Gfragments/s RPCF visibility (k x k PCF over RSMSS), same frames, one launch per frame",
+            "k": k, "value": fps(ms), "ms_per_step": ms, "launches_per_step": 2 * frames if k > 1 else frames,
+            "rsmss_same_launches": {"value": fps(ms_rsmss), "ms_per_step": ms_rsmss},
+            "samples_per_fragment": k * k}
 
 
 # -------------------------------------------------------------- reference --
