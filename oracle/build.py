@@ -8,7 +8,7 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["rbsm_oracle.c"]
+SOURCES = ["rbsm_oracle.c", "shadow_map_oracle.c"]
 LIB_NAME = "liboracle_rbsm.so"
 CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
           "-Wall", "-Wextra"]

@@ -34,6 +34,11 @@ def _load():
             ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
             ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]
+        lib.oracle_shadow_map.restype = ctypes.c_int
+        lib.oracle_shadow_map.argtypes = [
+            ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+            ctypes.c_double, ctypes.c_float]
         lib.oracle_features.restype = ctypes.c_int
         lib.oracle_features.argtypes = [
             ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
@@ -97,6 +102,28 @@ def rpcf(depth, x, y, z, k=3, max_dist=MAXDIST):
     if rc != 0:
         raise ValueError("oracle_rpcf rejected its arguments (rc=%d)" % rc)
     return vis
+
+
+def shadow_map(width, height, rects, rect_depth, spheres, zscale, ground=1.0):
+    """Shadow map (float32, (height, width)) of analytic occluders by brute
+    force (oracle/shadow_map_oracle.c): every texel centre against every
+    occluder, smallest depth, `ground` where nothing covers it.
+    rects: (n, 6) float64 cx cy ux uy ha hb; rect_depth: (n,) float32;
+    spheres: (m, 4) float64 cx cy R centre-depth."""
+    lib = _load()
+    rects = np.ascontiguousarray(np.asarray(rects, np.float64).reshape(-1, 6))
+    rect_depth = np.ascontiguousarray(np.asarray(rect_depth, np.float32).reshape(-1))
+    spheres = np.ascontiguousarray(np.asarray(spheres, np.float64).reshape(-1, 4))
+    if rect_depth.shape[0] != rects.shape[0]:
+        raise ValueError("one depth per rectangle")
+    depth = np.empty((height, width), np.float32)
+    rc = lib.oracle_shadow_map(depth.ctypes.data, int(width), int(height), int(width),
+                               _ptr(rects) if len(rects) else None, _ptr(rect_depth) if len(rects) else None,
+                               len(rects), _ptr(spheres) if len(spheres) else None, len(spheres),
+                               float(zscale), float(ground))
+    if rc != 0:
+        raise ValueError("oracle_shadow_map rejected its arguments (rc=%d)" % rc)
+    return depth
 
 
 def features(depth, x, y, z):
