@@ -289,6 +289,51 @@ int rbsm_batch_surrogate_counts(const void *workspace, uint64_t *accepted, uint6
 int rbsm_batch_status(const void *workspace, int *status);
 
 /*
+ * Shadow maps of analytic occluders: the light pass that produces SM, the
+ * input of Listing 1 (the paper rasterises it with the graphics pipeline;
+ * this library writes it with a CUDA kernel, for maps generated per frame).
+ * An orthographic light looks down the depth axis; texel (i, j) point-
+ * samples (i + 0.5, j + 0.5) and stores the smallest depth of the occluders
+ * covering that point, else `ground`:
+ *   rectangle: with p = point - (cx, cy), covered when |p . (ux, uy)| <= ha
+ *     and |p . (-uy, ux)| <= hb; its depth is `depth`;
+ *   sphere: covered when |p|^2 <= radius^2 (p from its centre); depth
+ *     centre_depth - sqrt(radius^2 - |p|^2) / zscale, rounded to float32.
+ * Every operation is a separate IEEE double operation in the order written
+ * (no fused multiply-add), so the map is bit-exact on any host.
+ * Occluder arrays are device memory owned by the caller; depth is a device
+ * map of width x height floats with `pitch` floats between rows.
+ * Errors: RBSM_ERR_ARG for NULL pointers with counts > 0, counts < 0,
+ * width or height outside 1..RBSM_MAX_EXTENT, pitch < width, zscale <= 0,
+ * flags != 0; RBSM_ERR_CUDA when the launch fails.
+ */
+typedef struct {
+    double cx, cy;                 /* centre, texel units */
+    double ux, uy;                 /* axis (unit length) */
+    double ha, hb;                 /* half extents along and across the axis */
+    float depth;
+    float reserved;                /* 0 */
+} rbsm_rect;
+
+typedef struct {
+    double cx, cy, radius;         /* texel units */
+    double centre_depth;
+} rbsm_sphere;
+
+typedef struct {
+    const rbsm_rect *rects;
+    int32_t n_rects;
+    const rbsm_sphere *spheres;
+    int32_t n_spheres;
+    double zscale;                 /* depth units per texel for the sphere caps */
+    float ground;                  /* depth of a texel nothing covers */
+    int32_t flags;                 /* reserved, 0 */
+} rbsm_occluders;
+
+int rbsm_shadow_map(const rbsm_occluders *occ, float *depth, int32_t width, int32_t height, int64_t pitch,
+                    void *stream);
+
+/*
  * Host-resident batches: the stager (this library's addition; the paper
  * evaluates fragments where the renderer produced them, on the GPU, and has
  * no host-side interface).

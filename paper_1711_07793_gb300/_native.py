@@ -74,6 +74,16 @@ class rbsm_stager_desc(ctypes.Structure):
                 ("flags", ctypes.c_int32)]
 
 
+class rbsm_occluders(ctypes.Structure):
+    _fields_ = [("rects", ctypes.c_void_p), ("n_rects", ctypes.c_int32), ("spheres", ctypes.c_void_p),
+                ("n_spheres", ctypes.c_int32), ("zscale", ctypes.c_double), ("ground", ctypes.c_float),
+                ("flags", ctypes.c_int32)]
+
+
+RBSM_RECT_BYTES = 56
+RBSM_SPHERE_BYTES = 32
+
+
 class RBSMError(RuntimeError):
     def __init__(self, fn, code, cuda_error=0):
         msg = "%s failed: %s (%d)" % (fn, status_string(code), code)
@@ -96,6 +106,8 @@ def _declare(lib):
         f.argtypes = [_P(rbsm_map), _P(rbsm_frags), vp, vp, _P(rbsm_params), vp]
     lib.rbsm_rpcf.restype = i32
     lib.rbsm_rpcf.argtypes = [_P(rbsm_map), _P(rbsm_frags), vp, ctypes.c_int32, _P(rbsm_params), vp]
+    lib.rbsm_shadow_map.restype = i32
+    lib.rbsm_shadow_map.argtypes = [_P(rbsm_occluders), vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, vp]
     lib.rbsm_map_texture_create.restype = i32
     lib.rbsm_map_texture_create.argtypes = [_P(rbsm_map), _P(ctypes.c_uint64)]
     lib.rbsm_map_texture_destroy.restype = i32

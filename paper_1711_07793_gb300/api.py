@@ -395,3 +395,44 @@ class Stager:
             self.close()
         except Exception:
             pass
+
+
+class DeviceOccluders:
+    """Analytic occluders of the light pass in device memory (rbsm_rect /
+    rbsm_sphere arrays): rects (n, 6) float64 cx cy ux uy ha hb with depths
+    (n,) float32, spheres (m, 4) float64 cx cy radius centre-depth."""
+
+    def __init__(self, rects, rect_depth, spheres, device=None):
+        import numpy as np
+        rects = np.asarray(rects, np.float64).reshape(-1, 6)
+        rect_depth = np.asarray(rect_depth, np.float32).reshape(-1)
+        spheres = np.asarray(spheres, np.float64).reshape(-1, 4)
+        if rect_depth.shape[0] != rects.shape[0]:
+            raise ValueError("one depth per rectangle")
+        rt = np.zeros(len(rects), np.dtype([("g", np.float64, 6), ("depth", np.float32), ("reserved", np.float32)]))
+        rt["g"] = rects
+        rt["depth"] = rect_depth
+        assert rt.dtype.itemsize == N.RBSM_RECT_BYTES
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.n_rects, self.n_spheres = len(rects), len(spheres)
+        self.rects = torch.from_numpy(rt.view(np.uint8).reshape(-1).copy()).to(dev)
+        self.spheres = torch.from_numpy(np.ascontiguousarray(spheres).view(np.uint8).reshape(-1).copy()).to(dev)
+
+    def desc(self, zscale, ground=1.0):
+        return N.rbsm_occluders(self.rects.data_ptr() if self.n_rects else None, self.n_rects,
+                                self.spheres.data_ptr() if self.n_spheres else None, self.n_spheres,
+                                float(zscale), float(ground), 0)
+
+
+def rbsm_shadow_map(occ, width, height, zscale, ground=1.0, out=None, stream=None):
+    """Shadow map of DeviceOccluders `occ` (rbsm_shadow_map): a (height,
+    width) float32 CUDA tensor, or `out` (rows contiguous, pitch >= width)."""
+    if out is None:
+        out = torch.empty((int(height), int(width)), dtype=torch.float32, device=occ.rects.device)
+    elif (not out.is_cuda or out.dtype != torch.float32 or out.dim() != 2 or out.stride(1) != 1
+          or tuple(out.shape) != (int(height), int(width))):
+        raise ValueError("out must be a (height, width) float32 CUDA tensor with contiguous rows")
+    d = occ.desc(zscale, ground)
+    N.check("rbsm_shadow_map", N.lib().rbsm_shadow_map(ctypes.byref(d), ctypes.c_void_p(out.data_ptr()), int(width),
+                                                       int(height), out.stride(0), _stream_handle(stream)))
+    return out

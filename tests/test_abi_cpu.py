@@ -49,6 +49,8 @@ int main(void) {
          offsetof(rbsm_batch, ctas_per_sm));
   printf("%zu %zu %zu %zu\n", sizeof(rbsm_stager_desc), offsetof(rbsm_stager_desc, max_width),
          offsetof(rbsm_stager_desc, slots), offsetof(rbsm_stager_desc, flags));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(rbsm_rect), sizeof(rbsm_sphere), sizeof(rbsm_occluders),
+         offsetof(rbsm_occluders, zscale), offsetof(rbsm_occluders, flags));
   return 0;
 }
 ''')
@@ -62,6 +64,9 @@ int main(void) {
                      ctypes.sizeof(N.rbsm_job), ctypes.sizeof(N.rbsm_batch)]
     assert offs == [N.rbsm_job.frags.offset, N.rbsm_job.vis_silhouette.offset, N.rbsm_job.codes.offset,
                     N.rbsm_batch.jobs.offset, N.rbsm_batch.params.offset, N.rbsm_batch.ctas_per_sm.offset]
+    oc = [int(v) for v in lines[3].split()]
+    assert oc == [N.RBSM_RECT_BYTES, N.RBSM_SPHERE_BYTES, ctypes.sizeof(N.rbsm_occluders),
+                  N.rbsm_occluders.zscale.offset, N.rbsm_occluders.flags.offset]
     st = [int(v) for v in lines[2].split()]
     assert st == [ctypes.sizeof(N.rbsm_stager_desc), N.rbsm_stager_desc.max_width.offset,
                   N.rbsm_stager_desc.slots.offset, N.rbsm_stager_desc.flags.offset]
@@ -124,6 +129,15 @@ def test_bad_arguments_are_rejected_before_any_cuda_call(native):
     assert lib.rbsm_stager_stats(None, B(i64), B(i64)) == N.RBSM_ERR_ARG
     assert lib.rbsm_stager_status(None, B(ctypes.c_int(0))) == N.RBSM_ERR_ARG
     assert lib.rbsm_stager_destroy(None) == N.RBSM_ERR_ARG
+    # the light pass: descriptor checks before any CUDA call
+    occ = N.rbsm_occluders(None, 0, None, 0, 1.0, 1.0, 0)
+    assert lib.rbsm_shadow_map(None, addr, 4, 4, 4, None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_shadow_map(B(occ), None, 4, 4, 4, None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_shadow_map(B(occ), addr, 4, 4, 3, None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_shadow_map(B(occ), addr, 0, 4, 4, None) == N.RBSM_ERR_ARG
+    for bad in (N.rbsm_occluders(None, 1, None, 0, 1.0, 1.0, 0), N.rbsm_occluders(None, 0, None, -1, 1.0, 1.0, 0),
+                N.rbsm_occluders(None, 0, None, 0, 0.0, 1.0, 0), N.rbsm_occluders(None, 0, None, 0, 1.0, 1.0, 2)):
+        assert lib.rbsm_shadow_map(B(bad), addr, 4, 4, 4, None) == N.RBSM_ERR_ARG
     assert lib.rbsm_status_string(N.RBSM_ERR_ARG) == b"invalid argument"
     assert lib.rbsm_version() >= 100
 
