@@ -54,6 +54,7 @@ def parse_args(argv=None):
     p.add_argument("--skip-cpu", action="store_true", help="profiling runs only")
     p.add_argument("--skip-learned", action="store_true", help="profiling runs only")
     p.add_argument("--skip-rpcf", action="store_true", help="profiling runs only")
+    p.add_argument("--skip-light", action="store_true", help="profiling runs only")
     p.add_argument("--guard-tau", type=float, default=0.05, help="surrogate guard (largest accepted error estimate)")
     p.add_argument("--texture", choices=["on", "off"], default="on",
                    help="read each map's four-neighbourhood with texture gathers (rbsm_map_texture_create)")
@@ -381,6 +382,11 @@ def run_ours(args, rank, world, local_rank):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
                "path": "rbsm_stager_run: pinned host maps/fragments/answers; fragment planes and map windows in"}
 
+    light = None
+    if not args.skip_light:
+        light = measure_light_pass(api, c5, maps, frames, n_frag, step, stream)
+        assert api.rbsm_batch_status(batch) == 0
+
     rpcf = None
     if not args.skip_rpcf:
         rpcf = measure_rpcf(api, texs or maps, xyz, frames, n_frag, args, stream)
@@ -418,6 +424,8 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "learned": learned,
         "rpcf": rpcf,
+        "light_pass": light["light_pass"] if light else None,
+        "frame_pipeline": light["frame_pipeline"] if light else None,
         "gpu_launches": args.steps,
         "clocks": clocks,
         "edge": {"unique_texels_per_frame": statistics.mean(h["U"] for h in host)},
@@ -529,6 +537,52 @@ def measure_rpcf(api, maps, xyz, frames, n_frag, args, stream, k=3):
             "k": k, "value": fps(ms), "ms_per_step": ms, "launches_per_step": 2 * frames if k > 1 else frames,
             "rsmss_same_launches": {"value": fps(ms_rsmss), "ms_per_step": ms_rsmss},
             "samples_per_fragment": k * k}
+
+
+def measure_light_pass(api, c5, maps, frames, n_frag, step_fn, stream):
+    """The light pass on the GPU (rbsm_shadow_map): the frames' 8192^2 maps
+    rasterised from their analytic occluders into the bench's own map
+    buffers (the kernel writes the generator's bytes, checked here on one
+    frame), alone and followed by the visibility step: the per-frame
+    pipeline with maps made on the device."""
+    import torch
+    occs = [api.DeviceOccluders(o.rects, o.rect_depth, o.spheres)
+            for o in (c5.occluders(f) for f in range(frames))]
+    size = c5.size
+    probe = api.rbsm_shadow_map(occs[frames - 1], size, size, float(size))
+    same = bool(torch.equal(probe, maps[frames - 1]))
+    del probe
+    steps = 5
+
+    def light():
+        for f in range(frames):
+            api.rbsm_shadow_map(occs[f], size, size, float(size), out=maps[f])
+
+    def pipeline():
+        light()
+        step_fn()
+
+    def timed(fn):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    ms_light = timed(light)
+    ms_pipe = timed(pipeline)
+    texels = frames * size * size
+    return {"light_pass": {"metric": "Gtexels/s shadow maps from analytic occluders (rbsm_shadow_map)",
+                           "value": texels / (ms_light * 1e-3) / 1e9, "ms_per_step": ms_light, "maps": frames,
+                           "map": size, "occluders_per_map": len(c5.base.rects) + len(c5.base.spheres),
+                           "bytes_equal_to_generator": same,
+                           "write_gbs": texels * 4 / (ms_light * 1e-3) / 1e9},
+            "frame_pipeline": {"metric": "Gfragments/s with the maps rasterised on the device in the step",
+                               "value": frames * n_frag / (ms_pipe * 1e-3) / 1e9, "ms_per_step": ms_pipe}}
 
 
 # -------------------------------------------------------------- reference --
