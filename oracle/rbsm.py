@@ -29,6 +29,9 @@ def _load():
             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
             ctypes.c_int32, ctypes.c_int32,
             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.oracle_project.restype = ctypes.c_int
+        lib.oracle_project.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         lib.oracle_rpcf.restype = ctypes.c_int
         lib.oracle_rpcf.argtypes = [
             ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
@@ -82,6 +85,21 @@ def evaluate(depth, x, y, z, mode, max_dist=MAXDIST, want_rd=False, want_nrd=Fal
     if want_nrd:
         out["nrd"] = nrd
     return out
+
+
+def project(gdepth, m):
+    """Light-space planes (x, y, z float32, fragment f = py * width + px) of
+    a depth buffer `gdepth` (height, width) through the 4 x 4 float32 matrix
+    `m` (reading R21 in rbsm_oracle.c)."""
+    lib = _load()
+    gdepth = np.ascontiguousarray(gdepth, dtype=np.float32)
+    m = np.ascontiguousarray(np.asarray(m, np.float32).reshape(4, 4))
+    h, w = gdepth.shape
+    out = [np.empty(h * w, np.float32) for _ in range(3)]
+    rc = lib.oracle_project(_ptr(gdepth), w, h, w, _ptr(m), _ptr(out[0]), _ptr(out[1]), _ptr(out[2]))
+    if rc != 0:
+        raise ValueError("oracle_project rejected its arguments (rc=%d)" % rc)
+    return tuple(out)
 
 
 def rpcf(depth, x, y, z, k=3, max_dist=MAXDIST):

@@ -309,6 +309,37 @@ int oracle_rbsm_eval(const float *depth, int32_t width, int32_t height, int64_t 
 }
 
 /* ------------------------------------------------------------------------
+ * Fragments from a depth buffer (the varying p of Listing 1, "the fragment
+ * transformed into light space", formed from a G-buffer).  Reading:
+ *   R21 pixel (px, py) of a width x height buffer holds depth d; with the
+ *       4 x 4 row-major float32 matrix M (screen to light clip space),
+ *       (X, Y, Z, W) = M (px + 0.5, py + 0.5, d, 1), each row summed left to
+ *       right, and p = (X / W, Y / W, Z / W), all single precision.
+ * Fragment f = py * width + px.  Writes the light-space planes; returns 0,
+ * or -1 on invalid arguments. */
+int oracle_project(const float *depth, int32_t width, int32_t height, int64_t pitch, const float *m,
+                   float *px_out, float *py_out, float *pz_out)
+{
+    if (!depth || !m || !px_out || !py_out || !pz_out || width < 1 || height < 1 || pitch < width)
+        return -1;
+    for (int64_t py = 0; py < height; ++py) {
+        for (int64_t px = 0; px < width; ++px) {
+            const float sx = (float)px + 0.5f, sy = (float)py + 0.5f, d = depth[py * pitch + px];
+            float v[4];
+            for (int r = 0; r < 4; ++r) {
+                const float *row = m + 4 * r;
+                v[r] = row[0] * sx + row[1] * sy + row[2] * d + row[3];
+            }
+            const int64_t f = py * width + px;
+            px_out[f] = v[0] / v[3];
+            py_out[f] = v[1] / v[3];
+            pz_out[f] = v[2] / v[3];
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
  * RPCF: percentage-closer filtering over the RSMSS answer (§5.3 suppresses
  * the skeleton artifacts of the filtered edges with PCF; the paper prints no
  * kernel for it).  Readings:

@@ -320,6 +320,10 @@ class Config5:
         du = self.parallax * math.tan(math.radians(C5_DEG_PER_FRAME * f))
         return self.base.shifted(du)
 
+    def gbuffer(self, z):
+        """(d, M) of this camera for light depths z (see gbuffer_of)."""
+        return gbuffer_of(self.hom, z, self.screen[0], self.screen[1], self.size, self.size)
+
     def frame(self, f, out_depth=None, out_xyz=None):
         occ = self.occluders(f)
         depth = raster(occ, self.size, self.size, self.size, out=out_depth)
@@ -328,6 +332,32 @@ class Config5:
                                   want_kind=True, out=out_xyz)
         return Frame("C5[%d]" % f, depth, x, y, z, self.screen,
                      {"window_side": self.window_side, "sphere_fraction": float(np.mean(kind > 0))})
+
+
+def gbuffer_of(hom, z, sw, sh, width, height):
+    """Depth-buffer form of a frame whose fragments come from the homography
+    `hom` (screen pixel centre -> texel units) with light depths `z`: the
+    4 x 4 float32 matrix M taking (px + 0.5, py + 0.5, d, 1) to light clip
+    space (rows x, y, z, w: the homography scaled to texture coordinates,
+    d itself, the homography's w) and the buffer d = z * w (float32,
+    (sh, sw)), so that (X / W, Y / W, Z / W) is the fragment again, up to
+    single-precision rounding."""
+    h = np.asarray(hom, np.float64)
+    m = np.zeros((4, 4), np.float64)
+    m[0, [0, 1, 3]] = h[0] / width
+    m[1, [0, 1, 3]] = h[1] / height
+    m[2, 2] = 1.0
+    m[3, [0, 1, 3]] = h[2]
+    m = m.astype(np.float32)
+    # w as the projection forms it (float32, row summed left to right, the
+    # d term 0), so that a fragment on the ground (z = 1) projects back to
+    # exactly z = 1 and keeps its shadow-test ties
+    u = np.arange(sw, dtype=np.float32) + np.float32(0.5)
+    v = np.arange(sh, dtype=np.float32) + np.float32(0.5)
+    w = (m[3, 0] * u[None, :] + m[3, 1] * v[:, None]) + np.float32(0.0)
+    w = w + m[3, 3]
+    d = np.asarray(z, np.float32).reshape(sh, sw) * w
+    return d.astype(np.float32), m
 
 
 C3_VIEWS = [(1280, 720), (1600, 900), (1920, 1080), (2560, 1080),
