@@ -140,6 +140,48 @@ int rsmss_filter(const rbsm_map *map, const rbsm_frags *frags, float *vis,
                  uint16_t *codes, const rbsm_params *params, void *stream);
 
 /*
+ * Visibility straight from depth buffers: the fragment's light-space
+ * position p (Listing 1's varying) is formed in the kernel instead of read.
+ * Pixel (px, py) of a job's buffer holds depth d; (X, Y, Z, W) =
+ * m (px + 0.5, py + 0.5, d, 1) with m its row-major 4 x 4
+ * screen-to-light-clip matrix, each row summed left to right in float32,
+ * and p = (X / W, Y / W, Z / W).  Fragment f = py * width + px then goes
+ * through the path of rbsm_visibility / rsmss_filter against the job's map:
+ * the answers are those of those calls on the projected planes, bit for
+ * bit, and 4 bytes per fragment are read instead of 12.  Every job is
+ * checked before the first launch; then each job runs as one launch, in
+ * order, on `stream`.
+ *   jobs: n_jobs (1..RBSM_GBUFFER_MAX_JOBS) descriptors, copied into the
+ *   launch; mode: RBSM_MODE_SILHOUETTE, _FILTER or _BOTH for every job;
+ *   vis_silhouette / vis_filter: width * height floats each as the mode
+ *   asks; codes: width * height uint16 (filter-mode codes for BOTH), given
+ *   for every job or for none.
+ * Errors: RBSM_ERR_ARG as for rbsm_visibility for each map, for a NULL or
+ * invalid depth buffer (width, height outside 1..RBSM_MAX_EXTENT,
+ * pitch < width), a bad mode or job count, a missing output or codes given
+ * for some jobs only; RBSM_ERR_CUDA when the launch fails.
+ */
+typedef struct {
+    const float *depth;            /* device, height rows of width floats */
+    int32_t width;
+    int32_t height;
+    int64_t pitch;                 /* floats between rows, >= width */
+    float m[16];                   /* row-major screen-to-light-clip matrix */
+} rbsm_gbuffer;
+
+typedef struct {
+    rbsm_map map;
+    rbsm_gbuffer gbuffer;
+    float *vis_silhouette;
+    float *vis_filter;
+    uint16_t *codes;
+} rbsm_gbuffer_job;
+
+#define RBSM_GBUFFER_MAX_JOBS 64
+int rbsm_visibility_gbuffer(const rbsm_gbuffer_job *jobs, int32_t n_jobs, int32_t mode,
+                            const rbsm_params *params, void *stream);
+
+/*
  * RPCF: percentage-closer filtering over the RSMSS answer (§5.3: the
  * skeleton artifacts along filtered edges are suppressed with PCF; the
  * paper prints no kernel for it).  For every fragment: the mean of the

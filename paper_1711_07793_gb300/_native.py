@@ -84,6 +84,19 @@ RBSM_RECT_BYTES = 56
 RBSM_SPHERE_BYTES = 32
 
 
+class rbsm_gbuffer(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_void_p), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("pitch", ctypes.c_int64), ("m", ctypes.c_float * 16)]
+
+
+class rbsm_gbuffer_job(ctypes.Structure):
+    _fields_ = [("map", rbsm_map), ("gbuffer", rbsm_gbuffer), ("vis_silhouette", ctypes.c_void_p),
+                ("vis_filter", ctypes.c_void_p), ("codes", ctypes.c_void_p)]
+
+
+RBSM_GBUFFER_MAX_JOBS = 64
+
+
 class RBSMError(RuntimeError):
     def __init__(self, fn, code, cuda_error=0):
         msg = "%s failed: %s (%d)" % (fn, status_string(code), code)
@@ -108,6 +121,9 @@ def _declare(lib):
     lib.rbsm_rpcf.argtypes = [_P(rbsm_map), _P(rbsm_frags), vp, ctypes.c_int32, _P(rbsm_params), vp]
     lib.rbsm_shadow_map.restype = i32
     lib.rbsm_shadow_map.argtypes = [_P(rbsm_occluders), vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, vp]
+    lib.rbsm_visibility_gbuffer.restype = i32
+    lib.rbsm_visibility_gbuffer.argtypes = [_P(rbsm_gbuffer_job), ctypes.c_int32, ctypes.c_int32,
+                                            _P(rbsm_params), vp]
     lib.rbsm_map_texture_create.restype = i32
     lib.rbsm_map_texture_create.argtypes = [_P(rbsm_map), _P(ctypes.c_uint64)]
     lib.rbsm_map_texture_destroy.restype = i32

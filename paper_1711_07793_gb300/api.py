@@ -436,3 +436,49 @@ def rbsm_shadow_map(occ, width, height, zscale, ground=1.0, out=None, stream=Non
     N.check("rbsm_shadow_map", N.lib().rbsm_shadow_map(ctypes.byref(d), ctypes.c_void_p(out.data_ptr()), int(width),
                                                        int(height), out.stride(0), _stream_handle(stream)))
     return out
+
+
+class GBufferJob:
+    """One (shadow map, depth buffer) pair of rbsm_visibility_gbuffer: `depth`
+    a map tensor or MapTexture, `gdepth` a (height, width) float32 CUDA
+    tensor with contiguous rows, `m` the 4 x 4 screen-to-light-clip matrix.
+    Answer planes (height * width) are allocated for the mode when not given."""
+
+    def __init__(self, depth, gdepth, m, mode=N.RBSM_MODE_BOTH, codes=False, vis_silhouette=None,
+                 vis_filter=None):
+        import numpy as np
+        if not isinstance(gdepth, torch.Tensor) or not gdepth.is_cuda or gdepth.dtype != torch.float32 \
+                or gdepth.dim() != 2 or gdepth.stride(1) != 1:
+            raise TypeError("gdepth must be a 2-D float32 CUDA tensor with contiguous rows")
+        self.depth, self.gdepth, self.mode = depth, gdepth, int(mode)
+        self.m = np.ascontiguousarray(np.asarray(m, np.float32).reshape(16))
+        n = gdepth.shape[0] * gdepth.shape[1]
+        dev = gdepth.device
+        if (mode & 1) and vis_silhouette is None:
+            vis_silhouette = torch.empty(n, dtype=torch.float32, device=dev)
+        if (mode & 2) and vis_filter is None:
+            vis_filter = torch.empty(n, dtype=torch.float32, device=dev)
+        if codes is True:
+            codes = torch.empty(n, dtype=torch.int16, device=dev)
+        self.vis_silhouette = vis_silhouette if mode & 1 else None
+        self.vis_filter = vis_filter if mode & 2 else None
+        self.codes = codes if isinstance(codes, torch.Tensor) else None
+
+    def desc(self):
+        h, w = self.gdepth.shape
+        g = N.rbsm_gbuffer(self.gdepth.data_ptr(), w, h, self.gdepth.stride(0),
+                           (ctypes.c_float * 16)(*self.m.tolist()))
+        ptr = lambda t: t.data_ptr() if t is not None else None
+        return N.rbsm_gbuffer_job(map_desc(self.depth), g, ptr(self.vis_silhouette), ptr(self.vis_filter),
+                                  ptr(self.codes))
+
+
+def rbsm_visibility_gbuffer(jobs, mode=N.RBSM_MODE_BOTH, max_dist=N.RBSM_MAXDIST_DEFAULT, stream=None):
+    """Visibility of every pixel of the jobs' depth buffers in one launch
+    (rbsm_visibility_gbuffer); each GBufferJob's answer planes are filled."""
+    jobs = list(jobs)
+    arr = (N.rbsm_gbuffer_job * len(jobs))(*[j.desc() for j in jobs])
+    p = _params(max_dist)
+    N.check("rbsm_visibility_gbuffer",
+            N.lib().rbsm_visibility_gbuffer(arr, len(jobs), int(mode), ctypes.byref(p), _stream_handle(stream)))
+    return jobs

@@ -51,6 +51,8 @@ int main(void) {
          offsetof(rbsm_stager_desc, slots), offsetof(rbsm_stager_desc, flags));
   printf("%zu %zu %zu %zu %zu\n", sizeof(rbsm_rect), sizeof(rbsm_sphere), sizeof(rbsm_occluders),
          offsetof(rbsm_occluders, zscale), offsetof(rbsm_occluders, flags));
+  printf("%zu %zu %zu %zu\n", sizeof(rbsm_gbuffer), offsetof(rbsm_gbuffer, m), sizeof(rbsm_gbuffer_job),
+         offsetof(rbsm_gbuffer_job, vis_filter));
   return 0;
 }
 ''')
@@ -64,6 +66,9 @@ int main(void) {
                      ctypes.sizeof(N.rbsm_job), ctypes.sizeof(N.rbsm_batch)]
     assert offs == [N.rbsm_job.frags.offset, N.rbsm_job.vis_silhouette.offset, N.rbsm_job.codes.offset,
                     N.rbsm_batch.jobs.offset, N.rbsm_batch.params.offset, N.rbsm_batch.ctas_per_sm.offset]
+    gbl = [int(v) for v in lines[4].split()]
+    assert gbl == [ctypes.sizeof(N.rbsm_gbuffer), N.rbsm_gbuffer.m.offset, ctypes.sizeof(N.rbsm_gbuffer_job),
+                   N.rbsm_gbuffer_job.vis_filter.offset]
     oc = [int(v) for v in lines[3].split()]
     assert oc == [N.RBSM_RECT_BYTES, N.RBSM_SPHERE_BYTES, ctypes.sizeof(N.rbsm_occluders),
                   N.rbsm_occluders.zscale.offset, N.rbsm_occluders.flags.offset]
@@ -129,6 +134,19 @@ def test_bad_arguments_are_rejected_before_any_cuda_call(native):
     assert lib.rbsm_stager_stats(None, B(i64), B(i64)) == N.RBSM_ERR_ARG
     assert lib.rbsm_stager_status(None, B(ctypes.c_int(0))) == N.RBSM_ERR_ARG
     assert lib.rbsm_stager_destroy(None) == N.RBSM_ERR_ARG
+    # the depth-buffer path: argument checks before any CUDA call
+    m16 = (ctypes.c_float * 16)(*([1.0] + [0.0] * 4 + [1.0] + [0.0] * 4 + [1.0] + [0.0] * 4 + [1.0]))
+    gb = N.rbsm_gbuffer(addr, 4, 4, 4, m16)
+    GJ = lambda g=gb, sil=addr, fil=addr, cod=None: (N.rbsm_gbuffer_job * 1)(N.rbsm_gbuffer_job(good_map, g, sil,
+                                                                                                fil, cod))
+    assert lib.rbsm_visibility_gbuffer(None, 1, 3, B(p), None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_visibility_gbuffer(GJ(), 0, 3, B(p), None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_visibility_gbuffer(GJ(), 65, 3, B(p), None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_visibility_gbuffer(GJ(), 1, 0, B(p), None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_visibility_gbuffer(GJ(sil=None), 1, 1, B(p), None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_visibility_gbuffer(GJ(fil=None), 1, 2, B(p), None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_visibility_gbuffer(GJ(g=N.rbsm_gbuffer(addr, 4, 4, 3, m16)), 1, 3, B(p), None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_visibility_gbuffer(GJ(g=N.rbsm_gbuffer(None, 4, 4, 4, m16)), 1, 3, B(p), None) == N.RBSM_ERR_ARG
     # the light pass: descriptor checks before any CUDA call
     occ = N.rbsm_occluders(None, 0, None, 0, 1.0, 1.0, 0)
     assert lib.rbsm_shadow_map(None, addr, 4, 4, 4, None) == N.RBSM_ERR_ARG
