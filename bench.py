@@ -55,6 +55,7 @@ def parse_args(argv=None):
     p.add_argument("--skip-learned", action="store_true", help="profiling runs only")
     p.add_argument("--skip-rpcf", action="store_true", help="profiling runs only")
     p.add_argument("--skip-light", action="store_true", help="profiling runs only")
+    p.add_argument("--skip-gbuffer", action="store_true", help="profiling runs only")
     p.add_argument("--guard-tau", type=float, default=0.05, help="surrogate guard (largest accepted error estimate)")
     p.add_argument("--texture", choices=["on", "off"], default="on",
                    help="read each map's four-neighbourhood with texture gathers (rbsm_map_texture_create)")
@@ -387,6 +388,10 @@ def run_ours(args, rank, world, local_rank):
         light = measure_light_pass(api, c5, maps, frames, n_frag, step, stream)
         assert api.rbsm_batch_status(batch) == 0
 
+    gbuf = None
+    if not args.skip_gbuffer:
+        gbuf = measure_gbuffer(api, c5, texs or maps, host, frames, n_frag, stream)
+
     rpcf = None
     if not args.skip_rpcf:
         rpcf = measure_rpcf(api, texs or maps, xyz, frames, n_frag, args, stream)
@@ -424,6 +429,7 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "learned": learned,
         "rpcf": rpcf,
+        "gbuffer": gbuf,
         "light_pass": light["light_pass"] if light else None,
         "frame_pipeline": light["frame_pipeline"] if light else None,
         "gpu_launches": args.steps,
@@ -583,6 +589,36 @@ def measure_light_pass(api, c5, maps, frames, n_frag, step_fn, stream):
                            "write_gbs": texels * 4 / (ms_light * 1e-3) / 1e9},
             "frame_pipeline": {"metric": "Gfragments/s with the maps rasterised on the device in the step",
                                "value": frames * n_frag / (ms_pipe * 1e-3) / 1e9, "ms_per_step": ms_pipe}}
+
+
+def measure_gbuffer(api, c5, maps, host, frames, n_frag, stream):
+    """The depth-buffer path (rbsm_visibility_gbuffer): the frames' camera
+    written as one depth plane and a 4 x 4 matrix each, p projected in the
+    kernel; one call (one launch per frame) per step, mode BOTH."""
+    import torch
+    dev = maps[0].depth.device if hasattr(maps[0], "depth") else maps[0].device
+    jobs = []
+    for f in range(frames):
+        d, m = c5.gbuffer(host[f]["xyz"][2].numpy())
+        jobs.append(api.GBufferJob(maps[f], torch.from_numpy(d).to(dev), m, mode=3))
+    steps = 10
+
+    def run():
+        api.rbsm_visibility_gbuffer(jobs)
+
+    for _ in range(3):
+        run()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"metric": "Gfragments/s visibility from depth buffers (p projected in the kernel), mode both",
+            "value": frames * n_frag / (ms * 1e-3) / 1e9, "ms_per_step": ms, "launches_per_step": frames,
+            "input_bytes_per_fragment": 4}
 
 
 # -------------------------------------------------------------- reference --
