@@ -56,6 +56,7 @@ def parse_args(argv=None):
     p.add_argument("--skip-rpcf", action="store_true", help="profiling runs only")
     p.add_argument("--skip-light", action="store_true", help="profiling runs only")
     p.add_argument("--skip-gbuffer", action="store_true", help="profiling runs only")
+    p.add_argument("--skip-sweep", action="store_true", help="profiling runs only")
     p.add_argument("--guard-tau", type=float, default=0.05, help="surrogate guard (largest accepted error estimate)")
     p.add_argument("--texture", choices=["on", "off"], default="on",
                    help="read each map's four-neighbourhood with texture gathers (rbsm_map_texture_create)")
@@ -388,6 +389,10 @@ def run_ours(args, rank, world, local_rank):
         light = measure_light_pass(api, c5, maps, frames, n_frag, step, stream)
         assert api.rbsm_batch_status(batch) == 0
 
+    sweep = None
+    if not args.skip_sweep:
+        sweep = measure_maxdist(api, texs or maps, xyz, frames, n_frag, args, stream)
+
     gbuf = None
     if not args.skip_gbuffer:
         gbuf = measure_gbuffer(api, c5, texs or maps, host, frames, n_frag, stream)
@@ -430,6 +435,7 @@ def run_ours(args, rank, world, local_rank):
         "learned": learned,
         "rpcf": rpcf,
         "gbuffer": gbuf,
+        "maxdist_sweep": sweep,
         "light_pass": light["light_pass"] if light else None,
         "frame_pipeline": light["frame_pipeline"] if light else None,
         "gpu_launches": args.steps,
@@ -619,6 +625,48 @@ def measure_gbuffer(api, c5, maps, host, frames, n_frag, stream):
     return {"metric": "Gfragments/s visibility from depth buffers (p projected in the kernel), mode both",
             "value": frames * n_frag / (ms * 1e-3) / 1e9, "ms_per_step": ms, "launches_per_step": frames,
             "input_bytes_per_fragment": 4}
+
+
+def measure_maxdist(api, maps, xyz, frames, n_frag, args, stream, caps=(8, 16, 32, 64)):
+    """The traversal cap as an accuracy / speed knob: for each cap, the
+    batched C5 step's rate and the largest filtering error against the
+    closed-form ramp on staircase edges of run lengths 8..64."""
+    import numpy as np
+    import torch
+    from tests import shapes
+    n = 512
+    offs = [((a + 0.5) / 16, (b + 0.5) / 16) for a in range(16) for b in range(16)]
+    stairs = []
+    for run_len in (8, 16, 32, 64):
+        depth = np.where(shapes.staircase_mask(n, run_len, 8, 40), shapes.BLOCKER, shapes.LIT).astype(np.float32)
+        X, Y = shapes.fragment_grid(80, n - 80, 34, n - 34, offs)
+        margin = (Y - 40) - (X - 8) / run_len
+        keep = (np.abs(margin) < 2.0) & (np.abs(margin) > 1e-6)
+        x, y = shapes.to_texcoords(X[keep], Y[keep], n, n)
+        stairs.append((run_len, torch.from_numpy(depth).to(xyz[0].device),
+                       [torch.from_numpy(np.ascontiguousarray(a)).to(xyz[0].device) for a in (x, y, np.ones_like(x))],
+                       np.clip(1.0 + margin[keep], 0.0, 1.0)))
+    out = []
+    for cap in caps:
+        jobs = [api.Job(k, xyz[k][0], xyz[k][1], xyz[k][2], mode=3) for k in range(frames)]
+        b = api.Batch(maps, jobs, max_dist=cap, tile_threads=args.tile_threads or 512, ctas_per_sm=args.ctas_per_sm)
+        for _ in range(3):
+            api.rbsm_batch_run(b)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(20):
+            api.rbsm_batch_run(b)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        errs = {}
+        for run_len, d, (xs, ys, zs), ramp in stairs:
+            fil, _ = api.rsmss_filter(d, xs, ys, zs, max_dist=cap)
+            errs[str(run_len)] = float(np.max(np.abs(fil.cpu().numpy().astype(np.float64) - ramp)))
+        out.append({"max_dist": cap, "value": frames * n_frag / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+                    "staircase_filter_max_err_by_run_length": errs})
+    return {"metric": "Gfragments/s (C5 step, mode both) and closed-form error per traversal cap", "caps": out}
 
 
 # -------------------------------------------------------------- reference --
