@@ -57,6 +57,8 @@ def parse_args(argv=None):
     p.add_argument("--skip-light", action="store_true", help="profiling runs only")
     p.add_argument("--skip-gbuffer", action="store_true", help="profiling runs only")
     p.add_argument("--skip-sweep", action="store_true", help="profiling runs only")
+    p.add_argument("--configs", action="store_true",
+                   help="one line per workload C1-C4 (GPU rate, roofline, oracle on 1 and all threads)")
     p.add_argument("--guard-tau", type=float, default=0.05, help="surrogate guard (largest accepted error estimate)")
     p.add_argument("--texture", choices=["on", "off"], default="on",
                    help="read each map's four-neighbourhood with texture gathers (rbsm_map_texture_create)")
@@ -669,6 +671,99 @@ def measure_maxdist(api, maps, xyz, frames, n_frag, args, stream, caps=(8, 16, 3
     return {"metric": "Gfragments/s (C5 step, mode both) and closed-form error per traversal cap", "caps": out}
 
 
+# ----------------------------------------------------------- per config --
+
+def oracle_rate(cases, threads, min_seconds):
+    """The oracle on `threads` host threads over (depth, x, y, z) cases, both
+    answers per fragment, cycling until min_seconds have passed."""
+    import numpy as np
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import rbsm as orc
+    done, k = 0, 0
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        while time.perf_counter() - t0 < min_seconds:
+            depth, x, y, z = cases[k % len(cases)]
+            k += 1
+            n = min(x.shape[0], 2_000_000)
+            bounds = np.linspace(0, n, threads + 1).astype(np.int64)
+
+            def work(t):
+                a, b = bounds[t], bounds[t + 1]
+                for mode in (orc.MODE_SILHOUETTE, orc.MODE_FILTER):
+                    orc.evaluate(depth, x[a:b], y[a:b], z[a:b], mode)
+                return b - a
+
+            done += sum(ex.map(work, range(threads)))
+    return done / (time.perf_counter() - t0) / 1e9
+
+
+def run_configs(args):
+    """One JSON line per workload C1-C4 (the C5 line is the default run):
+    the batched launch's rate and roofline fraction (autotuned shape, CUDA
+    graph, map textures, mode BOTH), the oracle's rate on 1 and on all host
+    threads (bounded samples of the same inputs) and, for C4, plain RSMSS
+    against the guarded surrogate."""
+    import numpy as np
+    import torch
+    from paper_1711_07793_gb300 import api
+    from paper_1711_07793_gb300 import build as lib_build
+    import rbsm_scenes as sc
+    lib_build.build()
+    device = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = load_peaks()
+    cores = os.cpu_count() or 1
+    workloads = [("C1 256^2, 320x240", lambda: [sc.config1(0)]),
+                 ("C2 2048^2, 1920x1080", lambda: [sc.config2(0)]),
+                 ("C3 16 maps (512^2..4096^2) x 8 views (720p..4K), 4 lights", lambda: sc.Config3(0)),
+                 ("C4 4096^2, 3840x2160", lambda: [sc.config4(0)])]
+    for name, make in workloads:
+        w = make()
+        if isinstance(w, sc.Config3):
+            maps_np = w.maps
+            parts = [(j.map_index, j.x, j.y, j.z) for j in w.jobs]
+        else:
+            maps_np = [f.depth for f in w]
+            parts = [(0, f.x, f.y, f.z) for f in w]
+        dmaps = [torch.from_numpy(m).to(device) for m in maps_np]
+        texs = [api.MapTexture(m) for m in dmaps]
+        planes = [(k, *(torch.from_numpy(np.ascontiguousarray(a)).to(device) for a in (x, y, z)))
+                  for k, x, y, z in parts]
+        jobs = [api.Job(k, x, y, z, mode=3) for k, x, y, z in planes]
+        batch = api.Batch(texs, jobs)
+        api.rbsm_batch_autotune(batch, repeats=3, cache=None)
+        graph = api.BatchGraph(batch)
+        for _ in range(5):
+            graph.launch()
+        steps = 50
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            graph.launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        n = sum(x.shape[0] for _, x, _, _ in parts)
+        texels = sum(unique_texels(x, y, maps_np[k].shape[0]) for k, x, y, _ in parts)
+        nbytes = BYTES_PER_FRAGMENT * n + BYTES_PER_TEXEL * texels
+        cases = [(maps_np[k], x, y, z) for k, x, y, z in parts]
+        line = {"workload": name, "fragments": n, "unit": UNIT,
+                "gpu": {"value": n / (ms * 1e-3) / 1e9, "ms_per_launch": ms,
+                        "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / peak, "peak_gbs": peak,
+                        "launch": {"tile_threads": batch.desc.tile_threads, "ctas_per_sm": batch.desc.ctas_per_sm}},
+                "cpu_oracle": {"threads_1": oracle_rate(cases, 1, 3.0),
+                               "threads_all": oracle_rate(cases, cores, 3.0), "cores": cores}}
+        if name.startswith("C4"):
+            line["learned"] = compare_learned(api, texs, [torch.stack([p[1], p[2], p[3]]) for p in planes],
+                                              1, n, args, stream)
+        graph.close()
+        for t in texs:
+            t.close()
+        print(json.dumps(line), flush=True)
+
+
 # -------------------------------------------------------------- reference --
 
 def run_reference(args, rank, world):
@@ -717,7 +812,9 @@ def main(argv=None):
         raise SystemExit("--gpus %d needs torchrun with %d processes" % (args.gpus, args.gpus))
     if args.warmup < 0 or args.steps < 1:
         raise SystemExit("--steps must be >= 1 and --warmup >= 0")
-    if args.impl == "reference":
+    if args.configs:
+        run_configs(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, world, local_rank)
