@@ -244,8 +244,9 @@ int rbsm_batch_workspace_size(const rbsm_batch *batch, size_t *bytes);
 
 /*
  * Enqueue one batched launch: a memset of the workspace followed by one
- * persistent kernel whose warps take chunks of 1024 fragments (8 tiles of
- * 128, in job order) from an atomic counter in the workspace.
+ * persistent kernel whose warps take chunks of 1 to 8 tiles of 128
+ * fragments (in job order; the chunk is as large as leaves every warp
+ * about eight claims) from an atomic counter in the workspace.
  * The descriptors are copied into the launch parameters, so the host arrays
  * may be reused as soon as the call returns.  Errors: RBSM_ERR_ARG as for
  * rbsm_visibility applied to every map and job, or a map index out of range;

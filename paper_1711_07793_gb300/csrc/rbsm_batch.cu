@@ -86,14 +86,21 @@ int shape_for(const BatchArgs &args, int ctas_per_sm, int umode, LaunchShape *ou
     const int sms = device_sm_count();
     if (sms <= 0)
         return cuda_fail(cudaErrorNoDevice);
-    const long long chunks = (args.total_tiles + kChunkTiles - 1) / kChunkTiles;
-    const long long blocks_needed = (chunks + kThreads / 32 - 1) / (kThreads / 32);
+    // about 8 claims per warp: chunks of 8 tiles when there is work enough,
+    // smaller ones (a power of two, down to 1) for launches of a few tiles
+    // per warp, where the last chunks would otherwise leave warps idle
     long long grid = (long long)sms * occ;
+    const long long warps = grid * (kThreads / 32);
+    int chunk = kMaxChunkTiles;
+    while (chunk > 1 && args.total_tiles < 8LL * chunk * warps)
+        chunk >>= 1;
+    const long long chunks = (args.total_tiles + chunk - 1) / chunk;
+    const long long blocks_needed = (chunks + kThreads / 32 - 1) / (kThreads / 32);
     if (grid > blocks_needed)
         grid = blocks_needed;
     if (grid < 1)
         grid = 1;
-    *out = LaunchShape{fn, kThreads, (unsigned)grid, smem};
+    *out = LaunchShape{fn, kThreads, (unsigned)grid, smem, chunk};
     return RBSM_OK;
 }
 
@@ -131,8 +138,9 @@ int launch_shape(const BatchArgs &args, int threads, int ctas_per_sm, LaunchShap
     }
 }
 
-int launch_kernel(const BatchArgs &args, const LaunchShape &sh, cudaStream_t stream)
+int launch_kernel(BatchArgs &args, const LaunchShape &sh, cudaStream_t stream)
 {
+    args.chunk_tiles = sh.chunk;
     sh.kernel<<<sh.grid, sh.threads, sh.smem, stream>>>(args);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
@@ -225,7 +233,7 @@ void bind_workspace(BatchArgs &a, void *ws)
 }
 
 // Enqueue the memset of the work counter / status word and the kernel.
-int enqueue_batch(const BatchArgs &a, const LaunchShape &sh, void *ws, cudaStream_t s)
+int enqueue_batch(BatchArgs &a, const LaunchShape &sh, void *ws, cudaStream_t s)
 {
     if (a.total_tiles == 0)
         return RBSM_OK;
@@ -287,7 +295,7 @@ int rbsm_batch_graph_create(const rbsm_batch *batch, void *workspace, size_t wor
     if ((rc = rbsm::check_workspace(workspace, workspace_bytes)) != RBSM_OK)
         return rc;
     rbsm::bind_workspace(args, workspace);
-    rbsm::LaunchShape sh{nullptr, 256, 1, 0};
+    rbsm::LaunchShape sh{nullptr, 256, 1, 0, 1};
     if (args.total_tiles > 0 && (rc = rbsm::launch_shape(args, threads, batch->ctas_per_sm, &sh)) != RBSM_OK)
         return rc;
     cudaStream_t s = nullptr;

@@ -19,6 +19,7 @@ struct LaunchShape {
     int threads;
     unsigned grid;
     size_t smem;
+    int chunk;                      // warp tiles per claim (BatchArgs::chunk_tiles)
 };
 
 // Validate a batch and fill the kernel arguments (everything but the
@@ -30,7 +31,8 @@ int check_workspace(const void *ws, size_t bytes);
 // Point the kernel arguments at the counter, status word and statistics of
 // a workspace.
 void bind_workspace(BatchArgs &a, void *ws);
-// Enqueue the workspace memset and the kernel (nothing for an empty batch).
-int enqueue_batch(const BatchArgs &a, const LaunchShape &sh, void *ws, cudaStream_t s);
+// Enqueue the workspace memset and the kernel (nothing for an empty batch);
+// sets a.chunk_tiles from the shape.
+int enqueue_batch(BatchArgs &a, const LaunchShape &sh, void *ws, cudaStream_t s);
 
 }  // namespace rbsm

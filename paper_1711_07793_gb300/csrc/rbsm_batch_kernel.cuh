@@ -39,10 +39,11 @@ struct BatchArgs {
     const void *mlp;                 // surrogate state block or nullptr
     float tau;                       // guard: largest accepted error estimate
     unsigned long long *stats;       // [0] surrogate answers, [1] fallbacks
+    int chunk_tiles;                 // warp tiles per claim of the work counter, 1..kMaxChunkTiles
 };
 
 constexpr size_t kWorkspaceBytes = 256;
-constexpr int kChunkTiles = 8;       // warp tiles per claim of the work counter
+constexpr int kMaxChunkTiles = 8;
 
 __device__ __forceinline__ int find_job(const BatchArgs &a, long long tile)
 {
@@ -183,7 +184,7 @@ constexpr size_t batch_smem_bytes()
     return sizeof(BatchSmem<kThreads, LEARNED>) + (LEARNED ? sizeof(LearnedSmem<kThreads>) : 0);
 }
 
-// Persistent warps claim chunks of kChunkTiles warp tiles from the work
+// Persistent warps claim chunks of chunk_tiles warp tiles from the work
 // counter (one atomic per 1024 fragments).  The claim of the next chunk is
 // issued when the current one starts, and its value is read only when the
 // warp gets there, so the atomic's latency hides behind eight tiles of work.
@@ -224,7 +225,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const __gri
     unsigned long long claim = 0;
     if (lane == 0)
         claim = atomicAdd(a.counter, 1ull);
-    long long tile = (long long)__shfl_sync(0xffffffffu, claim, 0) * kChunkTiles;
+    const int chunk = a.chunk_tiles;
+    long long tile = (long long)__shfl_sync(0xffffffffu, claim, 0) * chunk;
     if (tile >= total)
         return;
     if (lane == 0)
@@ -242,11 +244,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const __gri
     int queued = 0;
     for (;;) {
         long long nt;
-        if (in_chunk + 1 < kChunkTiles) {
+        if (in_chunk + 1 < chunk) {
             nt = tile + 1;
             in_chunk += 1;
         } else {
-            nt = (long long)__shfl_sync(0xffffffffu, claim, 0) * kChunkTiles;
+            nt = (long long)__shfl_sync(0xffffffffu, claim, 0) * chunk;
             in_chunk = 0;
             if (nt < total && lane == 0)
                 claim = atomicAdd(a.counter, 1ull);
