@@ -87,6 +87,7 @@ struct LearnedSmem {
     mlp::SmemWeights w;
     uint16_t feat[kThreads / 32][32 * mlp::kIn];
     float out[kThreads / 32][32 * mlp::kOut];
+    EdgeEntry fallback[kThreads / 32][64];      // guard-tripped fragments: < 32 left over + one round
 };
 
 // Drain rounds of up to 32 queued edge fragments with the surrogate: each
@@ -94,16 +95,33 @@ struct LearnedSmem {
 // the network on the 32 rows (two m16 tiles on the tensor cores), and each
 // fragment whose error estimate is within the guard takes the estimate,
 // clamped to [0, 1]; the others (and every fragment of a job that is not in
-// FILTER mode) take the exact walk.
+// FILTER mode) go to the warp's fallback queue, whose exact walks run in
+// rounds of 32 like the exact path's (walked in place, a round's few
+// fallbacks would keep most lanes idle through the walk).
 template <typename Jobs, int kThreads>
-__device__ __forceinline__ void drain_queue_learned(const Jobs &jobs, WarpQueue &wq, int &count, int max_dist,
-                                                    bool all, LearnedSmem<kThreads> &ls, int warp, float tau,
-                                                    unsigned long long *stats)
+__device__ __forceinline__ void drain_queue_learned(const Jobs &jobs, WarpQueue &wq, int &count, int &fb_count,
+                                                    int max_dist, bool all, LearnedSmem<kThreads> &ls, int warp,
+                                                    float tau, unsigned long long *stats)
 {
     const unsigned lane = lane_id();
+    const unsigned below = (1u << lane) - 1u;
     const int g = lane >> 2, t = lane & 3;
     uint16_t *feat = ls.feat[warp];
     float *yout = ls.out[warp];
+    EdgeEntry *fbq = ls.fallback[warp];
+    auto drain_fallback = [&](bool every) {
+        while (fb_count >= 32 || (every && fb_count > 0)) {
+            __syncwarp();
+            const int base = fb_count >= 32 ? fb_count - 32 : 0;
+            const int k = base + (int)lane;
+            if (k < fb_count) {
+                const EdgeEntry q = fbq[k];
+                resolve_entry(jobs((int)(q.bits_job >> 8)), q, max_dist);
+            }
+            __syncwarp();
+            fb_count = base;
+        }
+    };
     while (count >= 32 || (all && count > 0)) {
         __syncwarp();
         const int base = count >= 32 ? count - 32 : 0;
@@ -160,8 +178,10 @@ __device__ __forceinline__ void drain_queue_learned(const Jobs &jobs, WarpQueue 
                 }
             }
         }
-        if (valid && !accepted)
-            resolve_entry(o, q, max_dist);
+        const bool walk = valid && !accepted;
+        const unsigned walk_mask = __ballot_sync(0xffffffffu, walk);
+        if (walk)
+            fbq[fb_count + __popc(walk_mask & below)] = q;
         const unsigned acc_mask = __ballot_sync(0xffffffffu, accepted);
         const unsigned fb_mask = __ballot_sync(0xffffffffu, use_net && !accepted);
         if (lane == 0 && (acc_mask | fb_mask)) {
@@ -169,8 +189,11 @@ __device__ __forceinline__ void drain_queue_learned(const Jobs &jobs, WarpQueue 
             atomicAdd(&stats[1], (unsigned long long)__popc(fb_mask));
         }
         __syncwarp();
+        fb_count += __popc(walk_mask);
         count = base;
+        drain_fallback(false);
     }
+    drain_fallback(all);
 }
 
 template <int kThreads, bool LEARNED>
@@ -242,6 +265,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const __gri
     load_tile(t, lane, c);
     const BatchJobs jobs{&a};
     int queued = 0;
+    int fb_queued = 0;                         // learned variant: guard-tripped fragments waiting to walk
     for (;;) {
         long long nt;
         if (in_chunk + 1 < chunk) {
@@ -272,7 +296,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const __gri
         else
             classify_warp_tile<kFixedMode ? kFixedMode : 1, kFixedCodes>(a.maps[J.map], t, c, wq, queued);
         if (LEARNED)
-            drain_queue_learned<BatchJobs, kThreads>(jobs, wq, queued, a.max_dist, false, ls, warp, a.tau, a.stats);
+            drain_queue_learned<BatchJobs, kThreads>(jobs, wq, queued, fb_queued, a.max_dist, false, ls, warp, a.tau,
+                                                     a.stats);
         else
             drain_queue<BatchJobs, kFixedMode>(jobs, wq, queued, a.max_dist, false);
         if (!more)
@@ -283,7 +308,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const __gri
         c = cn;
     }
     if (LEARNED)
-        drain_queue_learned<BatchJobs, kThreads>(jobs, wq, queued, a.max_dist, true, ls, warp, a.tau, a.stats);
+        drain_queue_learned<BatchJobs, kThreads>(jobs, wq, queued, fb_queued, a.max_dist, true, ls, warp, a.tau,
+                                                 a.stats);
     else
         drain_queue<BatchJobs, kFixedMode>(jobs, wq, queued, a.max_dist, true);
 }
