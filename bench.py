@@ -393,7 +393,8 @@ def run_ours(args, rank, world, local_rank):
 
     sweep = None
     if not args.skip_sweep:
-        sweep = measure_maxdist(api, texs or maps, xyz, frames, n_frag, args, stream)
+        sweep = measure_maxdist(api, texs or maps, xyz, frames, n_frag, args, stream,
+                                (batch.desc.tile_threads, batch.desc.ctas_per_sm))
 
     gbuf = None
     if not args.skip_gbuffer:
@@ -629,7 +630,7 @@ def measure_gbuffer(api, c5, maps, host, frames, n_frag, stream):
             "input_bytes_per_fragment": 4}
 
 
-def measure_maxdist(api, maps, xyz, frames, n_frag, args, stream, caps=(8, 16, 32, 64)):
+def measure_maxdist(api, maps, xyz, frames, n_frag, args, stream, shape, caps=(8, 16, 32, 64)):
     """The traversal cap as an accuracy / speed knob: for each cap, the
     batched C5 step's rate and the largest filtering error against the
     closed-form ramp on staircase edges of run lengths 8..64."""
@@ -651,7 +652,7 @@ def measure_maxdist(api, maps, xyz, frames, n_frag, args, stream, caps=(8, 16, 3
     out = []
     for cap in caps:
         jobs = [api.Job(k, xyz[k][0], xyz[k][1], xyz[k][2], mode=3) for k in range(frames)]
-        b = api.Batch(maps, jobs, max_dist=cap, tile_threads=args.tile_threads or 512, ctas_per_sm=args.ctas_per_sm)
+        b = api.Batch(maps, jobs, max_dist=cap, tile_threads=shape[0], ctas_per_sm=shape[1])
         for _ in range(3):
             api.rbsm_batch_run(b)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -222,8 +222,10 @@ typedef struct {
     rbsm_params params;
     int32_t tile_threads;          /* CTA size: 128, 256 or 512 threads; 0 = default 256 */
     int32_t ctas_per_sm;           /* persistent CTAs per SM, 1..8; 0 = occupancy limit.  At
-                                    * 256 threads, 3 selects a variant compiled for 3 CTAs per
-                                    * SM (more registers per thread) */
+                                    * 256 threads the exact path has variants compiled for 3, 4
+                                    * and 5 CTAs per SM (80, 64, 48 registers per thread): 3
+                                    * selects the first, 1, 2 and 4 the second, 5 and up and 0
+                                    * the third */
     /* Learned penumbra (not in the paper): NULL = exact everywhere.  Given a
      * network state block (rbsm_mlp_state_bytes), FILTER-mode jobs answer
      * their edge fragments with the surrogate wherever its own error
@@ -299,9 +301,9 @@ int rbsm_batch_graph_launch(rbsm_graph graph, void *stream);
 int rbsm_batch_graph_destroy(rbsm_graph graph);
 
 /*
- * Autotuner of the batched launch shape.  Times 6 candidate (CTA size,
+ * Autotuner of the batched launch shape.  Times 7 candidate (CTA size,
  * CTAs per SM) pairs: 128 threads at its occupancy limit; 256 threads at 2,
- * 3 and 4 (occupancy limit) CTAs per SM; 512 threads at 1 and 2.
+ * 3, 4 and 5 (occupancy limit) CTAs per SM; 512 threads at 1 and 2.
  * Every warp works on its own 128-fragment tiles whatever the CTA size.
  * Each candidate gets `repeats` launches
  * each after one warm-up, on `stream`, and returns the fastest in *best.

@@ -69,6 +69,8 @@ BatchKernelFn kernel_for(int umode)
         return batch_kernel_256_4(LEARNED, umode);
     if (kThreads == 256 && kMinBlocks == 3)
         return batch_kernel_256_3(umode);
+    if (kThreads == 256 && kMinBlocks == 5)
+        return batch_kernel_256_5(umode);
     return batch_kernel_misc(kThreads, LEARNED);
 }
 
@@ -114,10 +116,11 @@ int uniform_mode(const BatchArgs &a)
     return 2 * m + c - 1;
 }
 
-// Kernel variant for a launch request.  At 256 threads, asking for 3 CTAs
-// per SM selects the variant whose registers are sized for 3 (80 per
-// thread instead of 64); the specialisations for a batch-uniform mode exist
-// for the 256-thread shapes.
+// Kernel variant for a launch request.  At 256 threads the exact path has
+// variants with registers sized for 3, 4 and 5 CTAs per SM (80, 64, 48 per
+// thread): asking for 3 selects the first, 5 or the occupancy limit (0) the
+// last, 1, 2 and 4 the middle one; the specialisations for a batch-uniform
+// mode exist for the 256-thread shapes.
 int launch_shape(const BatchArgs &args, int threads, int ctas_per_sm, LaunchShape *out)
 {
     const bool learned = args.mlp != nullptr;
@@ -134,6 +137,7 @@ int launch_shape(const BatchArgs &args, int threads, int ctas_per_sm, LaunchShap
     case 512: return shape_for<512, false, 2>(args, ctas_per_sm, 0, out);
     default:
         if (ctas_per_sm == 3) return shape_for<256, false, 3>(args, ctas_per_sm, um, out);
+        if (ctas_per_sm == 0 || ctas_per_sm >= 5) return shape_for<256, false, 5>(args, ctas_per_sm, um, out);
         return shape_for<256, false, 4>(args, ctas_per_sm, um, out);
     }
 }
@@ -382,7 +386,7 @@ int rbsm_batch_autotune(const rbsm_batch *batch, void *workspace, size_t workspa
         return rbsm::cuda_fail(e);
     }
     // candidate (CTA size, CTAs per SM); 0 = the variant's occupancy limit
-    const int cand[][2] = {{128, 0}, {256, 2}, {256, 3}, {256, 0}, {512, 1}, {512, 0}};
+    const int cand[][2] = {{128, 0}, {256, 2}, {256, 3}, {256, 4}, {256, 0}, {512, 1}, {512, 0}};
     const int n_cand = (int)(sizeof(cand) / sizeof(cand[0]));
     for (int ci = 0; ci < n_cand && rc == RBSM_OK; ++ci) {
         {

@@ -199,7 +199,43 @@ __device__ __forceinline__ void drain_queue_learned(const Jobs &jobs, WarpQueue 
 template <int kThreads, bool LEARNED>
 struct BatchSmem {
     WarpQueue queue[kThreads / 32];
+    float4 next[kThreads / 32][3][32];   // each warp's next tile: x, y, z, one float4 per lane and plane
 };
+
+// 16-byte asynchronous copy global -> shared (cp.async, cached in L2 only).
+__device__ __forceinline__ void copy_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// Start the copies of a tile's coordinates into the warp's buffer (vector
+// tiles; others are loaded directly when they come up).  Each lane copies
+// and later reads only its own float4 of each plane.
+__device__ __forceinline__ void stage_tile(const WarpTileIO &t, unsigned lane, float4 (&buf)[3][32])
+{
+    if (t.vec) {
+        copy_async16(&buf[0][lane], reinterpret_cast<const float4 *>(t.x + t.first) + lane);
+        copy_async16(&buf[1][lane], reinterpret_cast<const float4 *>(t.y + t.first) + lane);
+        copy_async16(&buf[2][lane], reinterpret_cast<const float4 *>(t.z + t.first) + lane);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// The staged tile's coordinates in registers (waits for the copies).
+__device__ __forceinline__ void fetch_tile(const WarpTileIO &t, unsigned lane, const float4 (&buf)[3][32],
+                                           LaneCoords &c)
+{
+    if (t.vec) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        const float4 vx = buf[0][lane], vy = buf[1][lane], vz = buf[2][lane];
+        c.x[0] = vx.x; c.x[1] = vx.y; c.x[2] = vx.z; c.x[3] = vx.w;
+        c.y[0] = vy.x; c.y[1] = vy.y; c.y[2] = vy.z; c.y[3] = vy.w;
+        c.z[0] = vz.x; c.z[1] = vz.y; c.z[2] = vz.z; c.z[3] = vz.w;
+    } else {
+        load_tile(t, lane, c);
+    }
+}
 
 template <int kThreads, bool LEARNED>
 constexpr size_t batch_smem_bytes()
@@ -208,11 +244,14 @@ constexpr size_t batch_smem_bytes()
 }
 
 // Persistent warps claim chunks of chunk_tiles warp tiles from the work
-// counter (one atomic per 1024 fragments).  The claim of the next chunk is
-// issued when the current one starts, and its value is read only when the
-// warp gets there, so the atomic's latency hides behind eight tiles of work.
-// While a warp works on one tile, the loads of its next tile's coordinates
-// are in flight (register double buffering).  Consecutive claims are
+// counter.  The claim of the next chunk is issued when the current one
+// starts, and its value is read only when the warp gets there, so the
+// atomic's latency hides behind a chunk of work.  While a warp works on one
+// tile, the asynchronous copies of its next tile's coordinates into the
+// warp's shared-memory buffer are in flight: the tile is read out of the
+// buffer into registers, the buffer is refilled with the next tile, and the
+// registers are classified (the prefetch holds no registers, which makes
+// room for 5 CTAs of 256 threads per SM).  Consecutive claims are
 // consecutive tiles of the job list, so warps working at the same time
 // share the L2 footprint of one region of one map.
 //
@@ -261,8 +300,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const __gri
     long long job_lo = a.jobs[job].tile_start;
     long long job_hi = job + 1 < a.n_jobs ? a.jobs[job + 1].tile_start : total;
     WarpTileIO t = job_tile(a.jobs[job], job, tile);
-    LaneCoords c;
-    load_tile(t, lane, c);
+    float4 (&buf)[3][32] = bs.next[warp];
+    stage_tile(t, lane, buf);
     const BatchJobs jobs{&a};
     int queued = 0;
     int fb_queued = 0;                         // learned variant: guard-tripped fragments waiting to walk
@@ -280,7 +319,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const __gri
         const bool more = nt < total;
         int njob = job;
         WarpTileIO tn;
-        LaneCoords cn;
+        LaneCoords c;
+        fetch_tile(t, lane, buf, c);
         if (more) {
             if (nt < job_lo || nt >= job_hi) {
                 njob = find_job(a, nt);
@@ -288,7 +328,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const __gri
                 job_hi = njob + 1 < a.n_jobs ? a.jobs[njob + 1].tile_start : total;
             }
             tn = job_tile(a.jobs[njob], njob, nt);
-            load_tile(tn, lane, cn);           // next tile's loads fly during this tile
+            stage_tile(tn, lane, buf);         // next tile's copies fly during this tile
         }
         const BatchJobDev &J = a.jobs[job];
         if (UMODE == 0)
@@ -305,7 +345,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const __gri
         tile = nt;
         job = njob;
         t = tn;
-        c = cn;
     }
     if (LEARNED)
         drain_queue_learned<BatchJobs, kThreads>(jobs, wq, queued, fb_queued, a.max_dist, true, ls, warp, a.tau,
@@ -319,6 +358,7 @@ using BatchKernelFn = void (*)(BatchArgs);
 // Kernel pointers of the instantiations (one function per translation unit).
 BatchKernelFn batch_kernel_256_4(bool learned, int umode);
 BatchKernelFn batch_kernel_256_3(int umode);
+BatchKernelFn batch_kernel_256_5(int umode);
 BatchKernelFn batch_kernel_misc(int threads, bool learned);
 
 }  // namespace rbsm
