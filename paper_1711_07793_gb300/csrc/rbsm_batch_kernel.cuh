@@ -202,41 +202,6 @@ struct BatchSmem {
     float4 next[kThreads / 32][3][32];   // each warp's next tile: x, y, z, one float4 per lane and plane
 };
 
-// 16-byte asynchronous copy global -> shared (cp.async, cached in L2 only).
-__device__ __forceinline__ void copy_async16(void *smem, const void *gmem)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
-}
-
-// Start the copies of a tile's coordinates into the warp's buffer (vector
-// tiles; others are loaded directly when they come up).  Each lane copies
-// and later reads only its own float4 of each plane.
-__device__ __forceinline__ void stage_tile(const WarpTileIO &t, unsigned lane, float4 (&buf)[3][32])
-{
-    if (t.vec) {
-        copy_async16(&buf[0][lane], reinterpret_cast<const float4 *>(t.x + t.first) + lane);
-        copy_async16(&buf[1][lane], reinterpret_cast<const float4 *>(t.y + t.first) + lane);
-        copy_async16(&buf[2][lane], reinterpret_cast<const float4 *>(t.z + t.first) + lane);
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-// The staged tile's coordinates in registers (waits for the copies).
-__device__ __forceinline__ void fetch_tile(const WarpTileIO &t, unsigned lane, const float4 (&buf)[3][32],
-                                           LaneCoords &c)
-{
-    if (t.vec) {
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        const float4 vx = buf[0][lane], vy = buf[1][lane], vz = buf[2][lane];
-        c.x[0] = vx.x; c.x[1] = vx.y; c.x[2] = vx.z; c.x[3] = vx.w;
-        c.y[0] = vy.x; c.y[1] = vy.y; c.y[2] = vy.z; c.y[3] = vy.w;
-        c.z[0] = vz.x; c.z[1] = vz.y; c.z[2] = vz.z; c.z[3] = vz.w;
-    } else {
-        load_tile(t, lane, c);
-    }
-}
-
 template <int kThreads, bool LEARNED>
 constexpr size_t batch_smem_bytes()
 {

@@ -87,14 +87,17 @@ struct PlainJobs {
 // (tile = global warp id + k * warps in the grid): consecutive warps hold
 // consecutive tiles, so the warps resident at one time gather from one
 // compact region of the shadow map.
+// The next tile waits in shared memory (cp.async), not in registers, which
+// leaves room for 5 CTAs of 256 threads per SM.
 template <int MODE, bool CODES, int kThreads>
-__global__ void __launch_bounds__(kThreads, 1024 / kThreads)
+__global__ void __launch_bounds__(kThreads, 1280 / kThreads)
 plain_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict__ y,
              const float *__restrict__ z, long long n, float *__restrict__ sil,
              float *__restrict__ fil, uint16_t *__restrict__ codes, int max_dist, bool vec_planes)
 {
     constexpr int kWarps = kThreads / 32;
     __shared__ WarpQueue wq[kWarps];
+    __shared__ float4 next[kWarps][3][32];
     const unsigned lane = lane_id();
     const int warp = threadIdx.x >> 5;
     const long long stride = (long long)gridDim.x * kWarps;
@@ -114,17 +117,18 @@ plain_kernel(const MapDev m, const float *__restrict__ x, const float *__restric
         return t;
     };
     WarpTileIO t = io_of(tile);
-    LaneCoords c;
-    load_tile(t, lane, c);
+    float4 (&buf)[3][32] = next[warp];
+    stage_tile(t, lane, buf);
     int queued = 0;
     for (;;) {
         const long long nt = tile + stride;
         const bool more = nt < tiles;
         WarpTileIO tn;
-        LaneCoords cn;
+        LaneCoords c;
+        fetch_tile(t, lane, buf, c);
         if (more) {
             tn = io_of(nt);
-            load_tile(tn, lane, cn);       // next tile's loads fly during this tile
+            stage_tile(tn, lane, buf);     // next tile's copies fly during this tile
         }
         classify_warp_tile<MODE, CODES>(m, t, c, wq[warp], queued);
         drain_queue(jobs, wq[warp], queued, max_dist, false);
@@ -132,7 +136,6 @@ plain_kernel(const MapDev m, const float *__restrict__ x, const float *__restric
             break;
         tile = nt;
         t = tn;
-        c = cn;
     }
     drain_queue(jobs, wq[warp], queued, max_dist, true);
 }
