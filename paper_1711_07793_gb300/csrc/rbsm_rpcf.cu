@@ -50,6 +50,7 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
     constexpr int kWarps = kThreads / 32;
     constexpr int R = (K - 1) / 2;
     __shared__ RpcfQueue wq[kWarps];
+    __shared__ float4 next[kWarps][3][32];     // the next tile's coordinates (cp.async)
     const unsigned lane = lane_id();
     const unsigned below = (1u << lane) - 1u;
     const int warp = threadIdx.x >> 5;
@@ -99,17 +100,18 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
         }
     };
     WarpTileIO t = io_of(tile);
-    LaneCoords c;
-    load_tile(t, lane, c);
+    float4 (&buf)[3][32] = next[warp];
+    stage_tile(t, lane, buf);
     int queued = 0;
     for (;;) {
         const long long nt = tile + stride;
         const bool more = nt < tiles;
         WarpTileIO tn;
-        LaneCoords cn;
+        LaneCoords c;
+        fetch_tile(t, lane, buf, c);
         if (more) {
             tn = io_of(nt);
-            load_tile(tn, lane, cn);       // next tile's loads fly during this tile
+            stage_tile(tn, lane, buf);     // next tile's copies fly during this tile
         }
 #pragma unroll 1
         for (int e = 0; e < kPerThread; ++e) {
@@ -163,7 +165,6 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
             break;
         tile = nt;
         t = tn;
-        c = cn;
     }
     drain(queued, true);
 }
