@@ -9,12 +9,22 @@
 // rectangle's own two axes, the disc against the box of texel centres, both
 // widened by half a texel), gathers the survivors in shared memory, and then
 // every thread tests its 4 texels against them.  Double precision is slow on
-// this GPU, so each test runs first in float, relative to the tile centre,
-// with an error bound: a float decision further than the bound from its
-// threshold is the exact one, and only texels within the bound of an edge
-// (and the cap depths of covered sphere texels) take the exact double
-// operations, in the defined order without contraction, so the map is
-// bit-exact.
+// this GPU, so the map's double-precision definition is reached mostly in
+// float:
+//   * the coverage tests run first in float, relative to the tile centre,
+//     with an error bound: a decision further than the bound from its
+//     threshold is the exact one;
+//   * a covered sphere texel's cap depth, RN32(c - sqrt(R^2 - rho^2) / z)
+//     of the double operations, is evaluated in float-float arithmetic
+//     (Knuth's TwoSum, the FMA product error, one Newton step for the
+//     square root) with a rigorous bound B on its distance from the double
+//     result; when the float-float value is further than B from every float
+//     rounding boundary, its rounding is the double result's;
+//   * everything else (texels within the bound of an edge, the few cap
+//     depths near a rounding boundary, scales z that are not powers of two)
+//     takes the exact double operations in the defined order without
+//     contraction,
+// so the map is bit-exact.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -45,6 +55,13 @@ struct SphereCand {
     double cx, cy, r, c;
     float dx0, dy0, r2f, e;                       // centre offset from the tile centre; rho^2 bound
     float dmin;                                   // no texel of the cap is nearer the light than this
+    // float-float data of the cap depth: tile centre - disc centre
+    // (dx0h + dx0l, dy0h + dy0l; within 2^-47 (|offset| + |centre|)),
+    // R^2 = r2h + r2l and c = ch + cl (within 2^-47 of the doubles), the
+    // centre's magnitude (cxa, cya); fast = 0 keeps every texel on the
+    // double operations
+    float dx0h, dx0l, dy0h, dy0l, r2h, r2l, ch, cl, cxa, cya;
+    int fast;
 };
 
 struct TileSmem {
@@ -64,7 +81,11 @@ struct FloatOcc {
     float cx, cy, ux, uy, ha, hb, ea;
 };
 struct FloatSph {
-    float cx, cy, r, ea;
+    float cx, cy, r, ea;         // cx, cy: the centre rounded to float
+    float cxl, cyl;              // what that rounding dropped, rounded (cx + cxl within 2^-48 |cx|)
+    float dmin;                  // no texel of the cap is nearer the light than this
+    float r2h, r2l, ch, cl;      // R^2 and c as float pairs (within 2^-47 of the doubles)
+    int fast;                    // R^2 and c in range for the float-float cap depth
 };
 
 // Float error bound of a quantity whose operands are at most `mag` in
@@ -81,18 +102,167 @@ __device__ __forceinline__ FloatOcc float_rect(const rbsm_rect &r)
                     (float)(fabs(r.cx) + fabs(r.cy)) * 2.384185791015625e-07f};    // 2^-22
 }
 
-__device__ __forceinline__ FloatSph float_sphere(const rbsm_sphere &c)
+__device__ __forceinline__ FloatSph float_sphere(const rbsm_sphere &c, double zscale)
 {
-    return FloatSph{(float)c.cx, (float)c.cy, (float)c.radius,
-                    (float)(fabs(c.cx) + fabs(c.cy) + c.radius) * 2.384185791015625e-07f};
+    FloatSph f;
+    f.cx = (float)c.cx;
+    f.cy = (float)c.cy;
+    f.cxl = (float)(c.cx - (double)f.cx);
+    f.cyl = (float)(c.cy - (double)f.cy);
+    f.r = (float)c.radius;
+    f.ea = (float)(fabs(c.cx) + fabs(c.cy) + c.radius) * 2.384185791015625e-07f;
+    // the cap's depth is at least c - R / zscale (R widened by 1e-6 for the
+    // rounding of R^2 and the square root), one float below
+    f.dmin = nextafterf((float)(c.centre_depth - c.radius * 1.000001 / zscale), -INFINITY);
+    f.r2h = (float)(c.radius * c.radius);
+    f.r2l = (float)fma(c.radius, c.radius, -(double)f.r2h);
+    f.ch = (float)c.centre_depth;
+    f.cl = (float)(c.centre_depth - (double)f.ch);
+    f.fast = f.r2h >= 1e-30f && f.r2h <= 1e30f && fabsf(f.ch) <= 1e30f;
+    return f;
+}
+
+// n as a float for 0 <= n < 2^23, from the bit pattern of 2^23 + n (the
+// int-to-float conversion runs on the slow FP64 pipe of this GPU).
+__device__ __forceinline__ float small_int_float(int n)
+{
+    return __fsub_rn(__int_as_float(0x4B000000 | n), 8388608.0f);
+}
+
+// Knuth's TwoSum: s + e == a + b exactly (round to nearest; the _rn
+// intrinsics are never contracted).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// The terms of R^2 - dx^2 that depend on the texel column only.
+struct CapColumn {
+    float s1;      // r2h - px, high part (TwoSum)
+    float low;     // its error + r2l - (dx^2 - px), rounded
+    float ex;      // r2h + dx^2 + mx^2, the column's share of the bound on A
+};
+
+__device__ __forceinline__ CapColumn cap_column(const SphereCand &c, float ox)
+{
+    // dx = ox + (dx0h + dx0l) as dxh + dxl (ox is exact, within 15.5)
+    float sh, sl, dxh, dxl;
+    two_sum(ox, c.dx0h, sh, sl);
+    two_sum(sh, __fadd_rn(sl, c.dx0l), dxh, dxl);
+    const float px = __fmul_rn(dxh, dxh);
+    const float pxe = __fmaf_rn(dxh, dxh, -px);                   // dxh^2 - px, exact
+    const float cxt = __fmul_rn(__fmul_rn(2.0f, dxh), dxl);       // 2 dxh dxl
+    CapColumn k;
+    float e1;
+    two_sum(c.r2h, -px, k.s1, e1);
+    k.low = __fsub_rn(__fsub_rn(__fadd_rn(e1, c.r2l), pxe), cxt);
+    const float mx = fabsf(ox) + fabsf(c.dx0h);
+    k.ex = c.r2h + px + mx * (mx + c.cxa);
+    return k;
+}
+
+// The cap depth of a texel by float-float arithmetic.  Returns 1 with *d =
+// RN32 of the double operations' depth (the texel is covered), 0 when the
+// double operations surely find the texel outside the disc, and -1 when
+// this cannot decide (the caller takes the double operations).
+//
+// Error analysis (u = 2^-24 float, 2^-53 double unit roundoff):
+//   A = R^2 - rho^2 (real) is held as ah + al with |ah + al - A| <= E_A =
+//   2^-41 (R^2 + dx^2 + dy^2 + mx (mx + |cx|) + my (my + |cy|)), mx =
+//   |ox| + |dx0h|: the split of R^2 loses 2^-47 R^2, the offset dx within
+//   2^-45 (mx + |cx|) (so dx^2 within 2^-44 mx (mx + |cx|)), the squares are
+//   exact (FMA) up to the 2 dxh dxl term (2^-47 dx^2) and the dropped dxl^2
+//   (2^-48 dx^2), and the seven low terms are summed with error at most 6u
+//   times their magnitudes (2^-43.1 of the squares).  When ah > 4 E_A and ah > 2^-40
+//   R^2, A > 2^-41 R^2, far above the 5 * 2^-53 R^2 that the double
+//   operations can move rho^2 <= R^2, so they find the texel covered.
+//   sqrt(ah + al) ~ r0 + corr with r0 = sqrt(ah) (correctly rounded) and
+//   one Newton step, corr = (ah - r0^2 + al) / (2 r0): error at most
+//   2^-42 r0 with a reciprocal good to 2^-21, plus E_A / r0 from A.  The
+//   scale 1/z is a power of two (exact in float), so the drop is
+//   (r0 + corr)/z exactly.  v = (ch - dh) + ((vl + cl) - dl) then carries
+//   2^-48 |c| from the split of c and 2^-22 (|vl| + |cl| + |dl|) from the
+//   two roundings.  The double operations themselves are within 2^-53 (|c|
+//   + 4 D + 8.2 R^2 / (r0 z)) of the real depth (D = the drop; rho^2 within
+//   4 roundings, A within 6u_d R^2, then the square root, the scale and the
+//   subtraction).  B below adds all of these with a factor 2 to spare, and
+//   the test asks for 2 B of room, so the decision holds under the rounding
+//   of B's own evaluation.
+__device__ __forceinline__ int cap_fast(const SphereCand &c, const CapColumn &k, float oy, float invf, float &d)
+{
+    float sh, sl, dyh, dyl;
+    two_sum(oy, c.dy0h, sh, sl);
+    two_sum(sh, __fadd_rn(sl, c.dy0l), dyh, dyl);
+    const float py = __fmul_rn(dyh, dyh);
+    const float pye = __fmaf_rn(dyh, dyh, -py);
+    const float cyt = __fmul_rn(__fmul_rn(2.0f, dyh), dyl);
+    float s2, e2, ah, al;
+    two_sum(k.s1, -py, s2, e2);
+    two_sum(s2, __fsub_rn(__fsub_rn(__fadd_rn(k.low, e2), pye), cyt), ah, al);
+    const float my = fabsf(oy) + fabsf(c.dy0h);
+    const float ea = 4.547473508864641e-13f * (k.ex + py + my * (my + c.cya));   // 2^-41
+    const float lim = 9.094947017729282e-13f * c.r2h;                     // 2^-40 R^2
+    if (!(ah > 4.0f * ea && ah > lim))
+        return ah < -(4.0f * ea + lim) ? 0 : -1;
+    const float r0 = __fsqrt_rn(ah);
+    const float rr = __fdividef(1.0f, r0);                                 // 1 / r0 within 2 ulp
+    const float corr = __fmul_rn(__fadd_rn(__fmaf_rn(-r0, r0, ah), al), __fmul_rn(0.5f, rr));
+    const float dh = __fmul_rn(r0, invf), dl = __fmul_rn(corr, invf);    // exact (power of two)
+    float vh, vl, f, r;
+    two_sum(c.ch, -dh, vh, vl);
+    two_sum(vh, __fsub_rn(__fadd_rn(vl, c.cl), dl), f, r);               // f + r = the float-float depth
+    const float B = 7.105427357601002e-15f * fabsf(c.ch)                                  // 2^-47
+                    + invf * (4.547473508864641e-13f * r0                                  // 2^-41
+                              + (1.01f * ea + 8.881784197001252e-16f * c.r2h) * rr)       // 2^-50
+                    + 2.384185791015625e-07f * (fabsf(vl) + fabsf(c.cl) + fabsf(dl))       // 2^-22
+                    + 7.52316384526264e-37f;                                               // 2^-120
+    // half the gap from f to the float on r's side: 2^(e-24) for f in
+    // [2^e, 2^(e+1)), 2^(e-25) below a power of two; positive normal f only
+    const unsigned bits = __float_as_uint(f), ef = bits >> 23;
+    if (ef < 26u || ef > 254u)
+        return -1;
+    const unsigned eh = ((bits & 0x7fffffu) == 0u && r < 0.0f) ? ef - 25u : ef - 24u;
+    if (!(__fsub_rn(__uint_as_float(eh << 23), fabsf(r)) > 2.0f * B))
+        return -1;
+    d = f;
+    return 1;
+}
+
+// The exact tests, out of line: the double-precision texel centre and the
+// double operations in the defined order, without contraction.  Kept out
+// of the tile loop so that it holds no double values (their conversions and
+// arithmetic run on the slow FP64 pipe) for the few texels that need them.
+__device__ __noinline__ bool rect_covers_exact(const RectCand &r, int i, int j)
+{
+    const double px = __dsub_rn((double)i + 0.5, r.cx), py = __dsub_rn((double)j + 0.5, r.cy);
+    const double s = __dadd_rn(__dmul_rn(px, r.ux), __dmul_rn(py, r.uy));
+    const double t = __dadd_rn(__dmul_rn(-px, r.uy), __dmul_rn(py, r.ux));
+    return fabs(s) <= r.ha && fabs(t) <= r.hb;
+}
+
+// The cap depth of texel (i, j), or +infinity when the disc does not cover
+// it (a value that lowers no depth, as an uncovered texel).
+__device__ __noinline__ float cap_depth_exact(const SphereCand &c, int i, int j, double inv_zscale, double zscale)
+{
+    const double dx = __dsub_rn((double)i + 0.5, c.cx), dy = __dsub_rn((double)j + 0.5, c.cy);
+    const double r2 = __dmul_rn(c.r, c.r);
+    const double rho2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    if (rho2 > r2)
+        return INFINITY;
+    const double root = __dsqrt_rn(__dsub_rn(r2, rho2));
+    const double drop = inv_zscale != 0.0 ? __dmul_rn(root, inv_zscale) : __ddiv_rn(root, zscale);
+    return __double2float_rn(__dsub_rn(c.c, drop));
 }
 
 // Cull occluders base + threadIdx.x against the tile centred at (tcx, tcy)
 // (float copies when the CTA holds them, else the double parameters) and
-// gather the survivors with their float pre-test data.
+// gather the survivors with their float pre-test data (and, for spheres
+// when `fast`, the float-float data of the cap depth).
 template <bool RECT>
 __device__ __forceinline__ void cull_chunk(const rbsm_occluders &occ, const FloatOcc *fo, const FloatSph *fs,
-                                           int base, float tcx, float tcy, TileSmem &sm)
+                                           int base, float tcx, float tcy, bool fast, TileSmem &sm)
 {
     constexpr float h = 0.5f * (kTile - 1);        // half size of the box of texel centres
     const int k = base + (int)threadIdx.x;
@@ -124,7 +294,7 @@ __device__ __forceinline__ void cull_chunk(const rbsm_occluders &occ, const Floa
                 rc.depth = r.depth;
             }
         } else {
-            const FloatSph f = fs ? fs[k] : float_sphere(occ.spheres[k]);
+            const FloatSph f = fs ? fs[k] : float_sphere(occ.spheres[k], occ.zscale);
             sc.dx0 = tcx - f.cx;
             sc.dy0 = tcy - f.cy;
             const float gx = fmaxf(fabsf(sc.dx0) - h, 0.0f), gy = fmaxf(fabsf(sc.dy0) - h, 0.0f);
@@ -137,8 +307,19 @@ __device__ __forceinline__ void cull_chunk(const rbsm_occluders &occ, const Floa
                 sc.e = err_bound(far * far) + 2.0f * far * f.ea;
                 // the cap's depth is at least c - R / zscale (R widened by
                 // 1e-6 for the rounding of R^2 and the square root), one float below
-                sc.dmin = nextafterf((float)(c.centre_depth - c.radius * 1.000001 / occ.zscale), -INFINITY);
+                sc.dmin = f.dmin;
                 sc.cx = c.cx; sc.cy = c.cy; sc.r = c.radius; sc.c = c.centre_depth;
+                // tile centre - disc centre in float-float: (tc - cx_f) exactly
+                // (TwoSum), then the dropped part of the centre
+                float a, e;
+                two_sum(tcx, -f.cx, a, e);
+                two_sum(a, __fsub_rn(e, f.cxl), sc.dx0h, sc.dx0l);
+                two_sum(tcy, -f.cy, a, e);
+                two_sum(a, __fsub_rn(e, f.cyl), sc.dy0h, sc.dy0l);
+                sc.r2h = f.r2h; sc.r2l = f.r2l; sc.ch = f.ch; sc.cl = f.cl;
+                sc.cxa = fabsf(f.cx);
+                sc.cya = fabsf(f.cy);
+                sc.fast = fast && f.fast && sc.cxa <= 1e15f && sc.cya <= 1e15f;
             }
         }
     }
@@ -169,48 +350,58 @@ __global__ void __launch_bounds__(kSmThreads) shadow_map_kernel(const rbsm_occlu
         for (int k = threadIdx.x; k < occ.n_rects; k += blockDim.x)
             fo[k] = float_rect(occ.rects[k]);
         for (int k = threadIdx.x; k < occ.n_spheres; k += blockDim.x)
-            fs[k] = float_sphere(occ.spheres[k]);
+            fs[k] = float_sphere(occ.spheres[k], occ.zscale);
         __syncthreads();
     }
     const FloatOcc *fop = copies ? fo : nullptr;
     const FloatSph *fsp = copies ? fs : nullptr;
+    // the float-float cap depth needs 1 / zscale exact in float
+    const bool fast = inv_zscale >= 7.888609052210118e-31 && inv_zscale <= 1.2676506002282294e30;   // 2^-100, 2^100
+    const float invf = (float)inv_zscale;
     const int tiles_x = (width + kTile - 1) / kTile;
-    const long long tiles = (long long)tiles_x * ((height + kTile - 1) / kTile);
+    const int tiles = tiles_x * ((height + kTile - 1) / kTile);     // <= 2^22
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     constexpr float h = 0.5f * (kTile - 1);
-    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const int i0 = (int)(tile % tiles_x) * kTile, j0 = (int)(tile / tiles_x) * kTile;
-        const float tcx = (float)i0 + 0.5f + h, tcy = (float)j0 + 0.5f + h;    // exact (< 2^23)
-        const int i = i0 + tx;
-        const double qx = __dadd_rn((double)i, 0.5);
-        const float ox = (float)tx - h;                // texel centre - tile centre (exact)
-        float best[4];
-        double qy[4];
+    // texel centre - tile centre, exact: ox for this thread's column, oy[p]
+    // for its rows ty + 8 p
+    const float ox = __fsub_rn(small_int_float(tx), h);
+    float oys[4];
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            best[p] = occ.ground;
-            qy[p] = (double)(j0 + ty + 8 * p) + 0.5;   // exact
+    for (int p = 0; p < 4; ++p)
+        oys[p] = __fsub_rn(small_int_float(ty + 8 * p), h);
+    // the tile's column and row, stepped by the grid stride (no division per tile)
+    int tcol = (int)blockIdx.x % tiles_x, trow = (int)blockIdx.x / tiles_x;
+    const int step_col = (int)gridDim.x % tiles_x, step_row = (int)gridDim.x / tiles_x;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int i0 = tcol * kTile, j0 = trow * kTile;
+        tcol += step_col;
+        trow += step_row;
+        if (tcol >= tiles_x) {
+            tcol -= tiles_x;
+            ++trow;
         }
+        // tile centre (i0 + 0.5 + 15.5, j0 + 16), exact (< 2^23)
+        const float tcx = small_int_float(i0 + kTile / 2), tcy = small_int_float(j0 + kTile / 2);
+        const int i = i0 + tx;
+        float best[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+            best[p] = occ.ground;
         for (int base = 0; base < occ.n_rects; base += kChunk) {
-            cull_chunk<true>(occ, fop, fsp, base, tcx, tcy, sm);
+            cull_chunk<true>(occ, fop, fsp, base, tcx, tcy, false, sm);
             for (int q = 0; q < sm.n; ++q) {
                 const RectCand &r = sm.r[q];
                 const float sx = ox * r.uxf, tx_ = -ox * r.uyf;
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
-                    const float oy = (float)(ty + 8 * p) - h;
+                    const float oy = oys[p];
                     const float sf = fabsf(r.s0 + (sx + oy * r.uyf));
                     const float tf = fabsf(r.t0 + (tx_ + oy * r.uxf));
                     if (sf > r.haf + r.es || tf > r.hbf + r.et || !(r.depth < best[p]))
                         continue;                      // surely outside, or it cannot lower the depth
                     bool in = sf < r.haf - r.es && tf < r.hbf - r.et;
-                    if (!in) {
-                        // near an edge: the exact test, double operations in the defined order
-                        const double px = __dsub_rn(qx, r.cx), py = __dsub_rn(qy[p], r.cy);
-                        const double s = __dadd_rn(__dmul_rn(px, r.ux), __dmul_rn(py, r.uy));
-                        const double t = __dadd_rn(__dmul_rn(-px, r.uy), __dmul_rn(py, r.ux));
-                        in = fabs(s) <= r.ha && fabs(t) <= r.hb;
-                    }
+                    if (!in)
+                        in = rect_covers_exact(r, i, j0 + ty + 8 * p);     // near an edge
                     if (in)
                         best[p] = r.depth;
                 }
@@ -218,24 +409,23 @@ __global__ void __launch_bounds__(kSmThreads) shadow_map_kernel(const rbsm_occlu
             __syncthreads();                       // survivors read before the next chunk
         }
         for (int base = 0; base < occ.n_spheres; base += kChunk) {
-            cull_chunk<false>(occ, fop, fsp, base, tcx, tcy, sm);
+            cull_chunk<false>(occ, fop, fsp, base, tcx, tcy, fast, sm);
             for (int q = 0; q < sm.n; ++q) {
                 const SphereCand &c = sm.s[q];
                 const float dxf = c.dx0 + ox;
-                const double dx = __dsub_rn(qx, c.cx);
-                const double r2 = __dmul_rn(c.r, c.r);
+                const CapColumn col = cap_column(c, ox);
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
-                    const float dyf = c.dy0 + ((float)(ty + 8 * p) - h);
+                    const float oy = oys[p];
+                    const float dyf = c.dy0 + oy;
                     if (!(c.dmin < best[p]) || dxf * dxf + dyf * dyf > c.r2f + c.e)
                         continue;                      // cannot lower the depth, or surely outside the disc
-                    const double dy = __dsub_rn(qy[p], c.cy);
-                    const double rho2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-                    if (rho2 > r2)
+                    float d = 0.0f;
+                    const int cap = c.fast ? cap_fast(c, col, oy, invf, d) : -1;
+                    if (cap == 0)
                         continue;
-                    const double root = __dsqrt_rn(__dsub_rn(r2, rho2));
-                    const double drop = inv_zscale != 0.0 ? __dmul_rn(root, inv_zscale) : __ddiv_rn(root, occ.zscale);
-                    const float d = __double2float_rn(__dsub_rn(c.c, drop));
+                    if (cap < 0)
+                        d = cap_depth_exact(c, i, j0 + ty + 8 * p, inv_zscale, occ.zscale);
                     if (d < best[p])
                         best[p] = d;
                 }

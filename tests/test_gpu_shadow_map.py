@@ -97,3 +97,24 @@ def test_full_size_c5_frame(api):
     ref = sc.raster(occ, c5.size, c5.size, c5.size)
     got = gpu_map(api, occ.rects, occ.rect_depth, occ.spheres, c5.size, c5.size, float(c5.size))
     assert same(got, ref)
+
+
+@pytest.mark.parametrize("zs", [1024.0, 64.0, 0.5, 1000.0, 3.0])
+def test_sphere_caps_against_the_oracle(api, zs):
+    """Cap depths of many large and tiny discs, with centre depths that put
+    caps below zero and above one, at power-of-two scales (the float-float
+    evaluation with its rounding-boundary fallback) and other scales (the
+    double operations throughout): bit-exact against the oracle."""
+    w = h = 1024
+    rng = np.random.default_rng(int(zs * 16))
+    n = 300
+    r = np.concatenate([rng.uniform(20, 300, 30), rng.uniform(0.3, 6, n - 30)])
+    c = r / zs + rng.uniform(0.01, 0.6, n)        # caps above zero
+    c[::10] = rng.uniform(-0.3, 0.3, len(c[::10]))
+    c[5::10] = r[5::10] / zs                       # the cap's centre at depth zero
+    sph = np.stack([rng.uniform(-50, w + 50, n), rng.uniform(-50, h + 50, n), r, c], 1)
+    sph[::11, 0:2] = np.floor(sph[::11, 0:2]) + 0.5
+    ref = orc.shadow_map(w, h, np.zeros((0, 6)), np.zeros(0, np.float32), sph, zs, ground=2.0)
+    got = gpu_map(api, np.zeros((0, 6)), np.zeros(0, np.float32), sph, w, h, zs, ground=2.0)
+    assert same(got, ref)
+    assert np.mean(ref < 2.0) > 0.15 and np.mean((ref > 0) & (ref < 2.0)) > 0.01
