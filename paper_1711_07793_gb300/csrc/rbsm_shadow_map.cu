@@ -260,7 +260,7 @@ __device__ __noinline__ float cap_depth_exact(const SphereCand &c, int i, int j,
 // (float copies when the CTA holds them, else the double parameters) and
 // gather the survivors with their float pre-test data (and, for spheres
 // when `fast`, the float-float data of the cap depth).
-template <bool RECT>
+template <bool RECT, bool COPIES>
 __device__ __forceinline__ void cull_chunk(const rbsm_occluders &occ, const FloatOcc *fo, const FloatSph *fs,
                                            int base, float tcx, float tcy, bool fast, TileSmem &sm)
 {
@@ -272,7 +272,7 @@ __device__ __forceinline__ void cull_chunk(const rbsm_occluders &occ, const Floa
     SphereCand sc;
     if (k < n) {
         if (RECT) {
-            const FloatOcc f = fo ? fo[k] : float_rect(occ.rects[k]);
+            const FloatOcc f = COPIES ? fo[k] : float_rect(occ.rects[k]);
             // tcx - cx and the projections in float: the error is at most
             // f.ea (centre rounding) + 2^-22 (|s0| + |t0|-size terms)
             const float dx = tcx - f.cx, dy = tcy - f.cy;
@@ -294,7 +294,7 @@ __device__ __forceinline__ void cull_chunk(const rbsm_occluders &occ, const Floa
                 rc.depth = r.depth;
             }
         } else {
-            const FloatSph f = fs ? fs[k] : float_sphere(occ.spheres[k], occ.zscale);
+            const FloatSph f = COPIES ? fs[k] : float_sphere(occ.spheres[k], occ.zscale);
             sc.dx0 = tcx - f.cx;
             sc.dy0 = tcy - f.cy;
             const float gx = fmaxf(fabsf(sc.dx0) - h, 0.0f), gy = fmaxf(fabsf(sc.dy0) - h, 0.0f);
@@ -337,24 +337,27 @@ __device__ __forceinline__ void cull_chunk(const rbsm_occluders &occ, const Floa
 }
 
 // inv_zscale: 1 / zscale when zscale is a power of two (dividing by it is
-// then the exact multiplication by its reciprocal), else 0.
+// then the exact multiplication by its reciprocal), else 0.  COPIES: the
+// CTA holds float copies of all occluders (neither kind has more than
+// kFloatCopies); a compile-time choice, so that the culling holds no
+// double-to-float conversions (slow FP64 pipe) when it reads the copies.
+template <bool COPIES>
 __global__ void __launch_bounds__(kSmThreads) shadow_map_kernel(const rbsm_occluders occ, float *__restrict__ depth,
                                                                 int width, int height, long long pitch,
                                                                 double inv_zscale)
 {
     __shared__ TileSmem sm;
-    __shared__ FloatOcc fo[kFloatCopies];
-    __shared__ FloatSph fs[kFloatCopies];
-    const bool copies = occ.n_rects <= kFloatCopies && occ.n_spheres <= kFloatCopies;
-    if (copies) {
+    __shared__ FloatOcc fo[COPIES ? kFloatCopies : 1];
+    __shared__ FloatSph fs[COPIES ? kFloatCopies : 1];
+    if (COPIES) {
         for (int k = threadIdx.x; k < occ.n_rects; k += blockDim.x)
             fo[k] = float_rect(occ.rects[k]);
         for (int k = threadIdx.x; k < occ.n_spheres; k += blockDim.x)
             fs[k] = float_sphere(occ.spheres[k], occ.zscale);
         __syncthreads();
     }
-    const FloatOcc *fop = copies ? fo : nullptr;
-    const FloatSph *fsp = copies ? fs : nullptr;
+    const FloatOcc *fop = fo;
+    const FloatSph *fsp = fs;
     // the float-float cap depth needs 1 / zscale exact in float
     const bool fast = inv_zscale >= 7.888609052210118e-31 && inv_zscale <= 1.2676506002282294e30;   // 2^-100, 2^100
     const float invf = (float)inv_zscale;
@@ -369,16 +372,25 @@ __global__ void __launch_bounds__(kSmThreads) shadow_map_kernel(const rbsm_occlu
 #pragma unroll
     for (int p = 0; p < 4; ++p)
         oys[p] = __fsub_rn(small_int_float(ty + 8 * p), h);
-    // the tile's column and row, stepped by the grid stride (no division per tile)
+    // the tile's column and row, stepped by the grid stride (no division per
+    // tile), and the offset of its first row in the map, stepped too: 64-bit
+    // integer multiplies share the slow FP64 pipe of this GPU
     int tcol = (int)blockIdx.x % tiles_x, trow = (int)blockIdx.x / tiles_x;
     const int step_col = (int)gridDim.x % tiles_x, step_row = (int)gridDim.x / tiles_x;
+    const long long tile_rows = (long long)kTile * pitch;
+    const long long step_rows = (long long)step_row * tile_rows;
+    long long row0 = (long long)trow * tile_rows + (long long)ty * pitch;   // this thread's first row
+    const long long pitch8 = pitch * 8;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int i0 = tcol * kTile, j0 = trow * kTile;
+        float *out = depth + row0 + i0 + tx;
         tcol += step_col;
         trow += step_row;
+        row0 += step_rows;
         if (tcol >= tiles_x) {
             tcol -= tiles_x;
             ++trow;
+            row0 += tile_rows;
         }
         // tile centre (i0 + 0.5 + 15.5, j0 + 16), exact (< 2^23)
         const float tcx = small_int_float(i0 + kTile / 2), tcy = small_int_float(j0 + kTile / 2);
@@ -388,7 +400,7 @@ __global__ void __launch_bounds__(kSmThreads) shadow_map_kernel(const rbsm_occlu
         for (int p = 0; p < 4; ++p)
             best[p] = occ.ground;
         for (int base = 0; base < occ.n_rects; base += kChunk) {
-            cull_chunk<true>(occ, fop, fsp, base, tcx, tcy, false, sm);
+            cull_chunk<true, COPIES>(occ, fop, fsp, base, tcx, tcy, false, sm);
             for (int q = 0; q < sm.n; ++q) {
                 const RectCand &r = sm.r[q];
                 const float sx = ox * r.uxf, tx_ = -ox * r.uyf;
@@ -409,7 +421,7 @@ __global__ void __launch_bounds__(kSmThreads) shadow_map_kernel(const rbsm_occlu
             __syncthreads();                       // survivors read before the next chunk
         }
         for (int base = 0; base < occ.n_spheres; base += kChunk) {
-            cull_chunk<false>(occ, fop, fsp, base, tcx, tcy, fast, sm);
+            cull_chunk<false, COPIES>(occ, fop, fsp, base, tcx, tcy, fast, sm);
             for (int q = 0; q < sm.n; ++q) {
                 const SphereCand &c = sm.s[q];
                 const float dxf = c.dx0 + ox;
@@ -435,9 +447,9 @@ __global__ void __launch_bounds__(kSmThreads) shadow_map_kernel(const rbsm_occlu
         if (i < width) {
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
-                const int j = j0 + ty + 8 * p;
-                if (j < height)
-                    depth[(long long)j * pitch + i] = best[p];
+                if (j0 + ty + 8 * p < height)
+                    *out = best[p];
+                out += pitch8;
             }
         }
     }
@@ -454,9 +466,11 @@ extern "C" int rbsm_shadow_map(const rbsm_occluders *occ, float *depth, int32_t 
         pitch < width || occ->n_rects < 0 || occ->n_spheres < 0 || (occ->n_rects > 0 && !occ->rects) ||
         (occ->n_spheres > 0 && !occ->spheres) || !(occ->zscale > 0.0) || occ->flags != 0)
         return RBSM_ERR_ARG;
-    static KernelSetup setup;
+    const bool copies = occ->n_rects <= kFloatCopies && occ->n_spheres <= kFloatCopies;
+    static KernelSetup setup_copies, setup_plain;
+    auto kern = copies ? shadow_map_kernel<true> : shadow_map_kernel<false>;
     int occupancy = 0;
-    int rc = setup.get(shadow_map_kernel, kSmThreads, 0, &occupancy);
+    int rc = (copies ? setup_copies : setup_plain).get(kern, kSmThreads, 0, &occupancy);
     if (rc != RBSM_OK)
         return rc;
     const int sms = device_sm_count();
@@ -468,8 +482,8 @@ extern "C" int rbsm_shadow_map(const rbsm_occluders *occ, float *depth, int32_t 
         grid = tiles;
     int e2 = 0;
     const double inv = std::frexp(occ->zscale, &e2) == 0.5 ? std::ldexp(1.0, 1 - e2) : 0.0;
-    shadow_map_kernel<<<(unsigned)grid, kSmThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-        *occ, depth, width, height, pitch, inv);
+    kern<<<(unsigned)grid, kSmThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(*occ, depth, width, height,
+                                                                                   pitch, inv);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return cuda_fail(e);

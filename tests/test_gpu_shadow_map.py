@@ -118,3 +118,21 @@ def test_sphere_caps_against_the_oracle(api, zs):
     got = gpu_map(api, np.zeros((0, 6)), np.zeros(0, np.float32), sph, w, h, zs, ground=2.0)
     assert same(got, ref)
     assert np.mean(ref < 2.0) > 0.15 and np.mean((ref > 0) & (ref < 2.0)) > 0.01
+
+
+@pytest.mark.parametrize("nr,ns", [(1100, 0), (0, 1100), (513, 1025)])
+def test_occluders_in_several_passes(api, nr, ns):
+    """More than one pass of occluders of a kind (512 each): the running
+    minimum is carried through the map between passes."""
+    w, h = 150, 130
+    rng = np.random.default_rng(nr * 7 + ns)
+    ang = rng.uniform(0, np.pi, nr)
+    rects = np.stack([rng.uniform(-10, w + 10, nr), rng.uniform(-10, h + 10, nr), np.cos(ang), np.sin(ang),
+                      rng.uniform(0.2, 12, nr), rng.uniform(0.2, 12, nr)], 1).reshape(-1, 6)
+    rdep = rng.uniform(0.05, 0.95, nr).astype(np.float32)
+    sph = np.stack([rng.uniform(-5, w + 5, ns), rng.uniform(-5, h + 5, ns), rng.uniform(0.3, 9, ns),
+                    rng.uniform(0.2, 0.9, ns)], 1).reshape(-1, 4)
+    ref = orc.shadow_map(w, h, rects, rdep, sph, 64.0, ground=0.99)
+    got = gpu_map(api, rects, rdep, sph, w, h, 64.0, ground=0.99)
+    assert same(got, ref)
+    assert np.mean(ref < 0.99) > 0.5
