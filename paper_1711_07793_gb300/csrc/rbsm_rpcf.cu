@@ -31,15 +31,64 @@ constexpr int kRpcfThreads = 256;
 constexpr float kFix = 33554432.0f;            // 2^25
 constexpr float kUnfix = 1.0f / 33554432.0f;   // 2^-25 (exact)
 constexpr uint32_t kNanFlag = 0x80000000u;     // above any sum (49 * 2^25 < 2^31): the mean is NaN
-constexpr int kRpcfQueueCap = 64;              // < 32 left over + one sample of every lane
-
+// Edge samples are queued per fragment element: for k <= 3 all of a lane's
+// edge samples at once (a warp prefix sum places them), so the queue holds
+// < 32 left over + k^2 samples of every lane; for larger k one sample
+// position at a time (a ballot each), < 32 + 32.
+template <int K>
 struct RpcfQueue {
-    EdgeEntry q[kRpcfQueueCap];
+    static constexpr int kCap = K <= 3 ? 32 * K * K + 32 : 64;
+    EdgeEntry q[kCap];
 };
 
 __device__ __forceinline__ uint32_t to_fix(float v)
 {
     return (uint32_t)__float2uint_rn(__fmul_rn(v, kFix));
+}
+
+// The shared block.  Sample (a, b)'s texel is clamp(floor(u + a)) with u + a
+// rounded to float; when every such floor is floor(u) + a (u + a can round
+// up to the next integer where it crosses a power of two) and the (K + 2)^2
+// block of texels around floor(u), floor(v) lies inside the map (no
+// clamping), all K^2 samples' four-neighbourhoods come from that one block:
+// ceil((K + 2) / 2)^2 texture gathers instead of 2 K^2, and one shadow test
+// (Eq. 1) per texel.  Other fragments take the per-sample path.
+template <int K>
+__device__ __forceinline__ bool block_ok(float u, float v, float uhi, float vhi)
+{
+    constexpr int R = (K - 1) / 2;
+    const float fu = floorf(u), fv = floorf(v);
+    bool ok = fu >= (float)(R + 1) && fu <= uhi && fv >= (float)(R + 1) && fv <= vhi;    // false for NaN
+#pragma unroll
+    for (int d = 1; d <= R; ++d) {
+        ok = ok && floorf(__fadd_rn(u, (float)d)) == fu + (float)d && floorf(__fadd_rn(u, (float)-d)) == fu - (float)d &&
+             floorf(__fadd_rn(v, (float)d)) == fv + (float)d && floorf(__fadd_rn(v, (float)-d)) == fv - (float)d;
+    }
+    return ok;
+}
+
+// Bit x of rows[y]: texel (floor(u) - R - 1 + x, floor(v) - R - 1 + y) is
+// lit for depth pz (Eq. 1).  Gather (X, Y) covers columns X - 1, X and rows
+// Y - 1, Y; components x = (lo col, hi row), y = (hi, hi), z = (hi, lo),
+// w = (lo, lo).
+template <int K>
+__device__ __forceinline__ void block_bits(const MapDev &m, float u, float v, float pz, uint32_t (&rows)[K + 2])
+{
+    constexpr int R = (K - 1) / 2, B = K + 2, G = (B + 1) / 2;
+    const float gx = floorf(u) - (float)R, gy = floorf(v) - (float)R;
+#pragma unroll
+    for (int y = 0; y < B; ++y)
+        rows[y] = 0u;
+#pragma unroll
+    for (int n = 0; n < G; ++n) {
+#pragma unroll
+        for (int c = 0; c < G; ++c) {
+            const float4 g = tex2Dgather<float4>(m.tex, gx + (float)(2 * c), gy + (float)(2 * n), 0);
+            rows[2 * n] |= ((uint32_t)!(pz > g.w) << (2 * c)) | ((uint32_t)!(pz > g.z) << (2 * c + 1));
+            if (2 * n + 1 < B)
+                rows[2 * n + 1] |= ((uint32_t)!(pz > g.x) << (2 * c)) | ((uint32_t)!(pz > g.y) << (2 * c + 1));
+        }
+    }
 }
 
 template <int K, int kThreads>
@@ -49,7 +98,7 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
 {
     constexpr int kWarps = kThreads / 32;
     constexpr int R = (K - 1) / 2;
-    __shared__ RpcfQueue wq[kWarps];
+    __shared__ RpcfQueue<K> wq[kWarps];
     __shared__ float4 next[kWarps][3][32];     // the next tile's coordinates (cp.async)
     const unsigned lane = lane_id();
     const unsigned below = (1u << lane) - 1u;
@@ -60,6 +109,9 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
     if (tile >= tiles)
         return;
     const float W = (float)m.width, H = (float)m.height;
+    // the largest floor(u), floor(v) whose block lies inside the map
+    const float uhi = (float)(m.width - R - 2), vhi = (float)(m.height - R - 2);
+    const bool tex = K > 1 && m.tex != 0;
     uint32_t *acc = reinterpret_cast<uint32_t *>(vis);
     auto io_of = [&](long long tl) {
         WarpTileIO t;
@@ -126,17 +178,35 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
             uint64_t edges = 0;
             uint32_t base = 0;
             float single = 0.0f;
+            if (tex && valid && block_ok<K>(u, v, uhi, vhi)) {
+                uint32_t rows[K + 2];
+                block_bits<K>(m, u, v, ze, rows);
+                // a row of samples at once: sample (a, b)'s texel is block
+                // (a + 1, b + 1); it is an edge sample where one of Listing
+                // 2's four neighbours differs from it, else it adds its
+                // shadow test
+                constexpr uint32_t mk = (1u << K) - 1u;
 #pragma unroll
-            for (int q = 0; q < K * K; ++q) {
-                FragResult r{0.0f, 0.0f, 0};
-                uint32_t bits = 0;
-                const bool edge = valid && classify_uv<2, false>(m, __fadd_rn(u, (float)(q % K - R)),
-                                                                 __fadd_rn(v, (float)(q / K - R)), ze, r, bits);
-                if (edge) {
-                    edges |= 1ull << q;
-                } else {
-                    base += r.fil != 0.0f ? (1u << 25) : 0u;
-                    single = r.fil;
+                for (int b = 0; b < K; ++b) {
+                    const uint32_t c = (rows[b + 1] >> 1) & mk;
+                    const uint32_t e = (c ^ (rows[b + 1] & mk)) | (c ^ ((rows[b + 1] >> 2) & mk)) |
+                                       (c ^ ((rows[b + 2] >> 1) & mk)) | (c ^ ((rows[b] >> 1) & mk));
+                    edges |= (uint64_t)e << (K * b);
+                    base += (uint32_t)__popc(c & ~e) << 25;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < K * K; ++q) {
+                    FragResult r{0.0f, 0.0f, 0};
+                    uint32_t bits = 0;
+                    const bool edge = valid && classify_uv<2, false>(m, __fadd_rn(u, (float)(q % K - R)),
+                                                                     __fadd_rn(v, (float)(q / K - R)), ze, r, bits);
+                    if (edge) {
+                        edges |= 1ull << q;
+                    } else {
+                        base += r.fil != 0.0f ? (1u << 25) : 0u;
+                        single = r.fil;
+                    }
                 }
             }
             // the base value is stored before any deferred sample of this
@@ -147,9 +217,32 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
                 else
                     acc[t.first + s] = base;
             }
-            // ... then the edge samples are queued, one sample index at a
-            // time, and walked whenever 32 are waiting
-            if (__any_sync(0xffffffffu, edges != 0)) {
+            // ... then the edge samples are queued and walked whenever 32
+            // are waiting
+            if (K <= 3) {
+                // all of the lane's edge samples, placed by a prefix sum
+                const uint32_t ne = (uint32_t)__popcll(edges);
+                uint32_t incl = ne;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const uint32_t t2 = __shfl_up_sync(0xffffffffu, incl, off);
+                    if ((int)lane >= off)
+                        incl += t2;
+                }
+                const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                if (total != 0u) {
+                    int pos = queued + (int)(incl - ne);
+                    uint64_t rest = edges;
+                    while (rest) {
+                        const int q = __ffsll((long long)rest) - 1;
+                        rest &= rest - 1;
+                        wq[warp].q[pos++] = EdgeEntry{(uint32_t)(t.first + s), (uint32_t)q};
+                    }
+                    queued += (int)total;
+                    drain(queued, false);
+                }
+            } else if (__any_sync(0xffffffffu, edges != 0)) {
+                // one sample position at a time
 #pragma unroll 1
                 for (int q = 0; q < K * K; ++q) {
                     const bool eq = (edges >> q) & 1ull;

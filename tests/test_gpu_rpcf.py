@@ -136,3 +136,30 @@ def test_full_size_frame_sampled(api):
     ref = orc.rpcf(depth, x[idx], y[idx], z[idx], k=3)
     assert np.abs(got[idx].astype(np.float64) - ref).max() <= TOL
     assert 0.0 < np.mean((ref > 0) & (ref < 1)) < 0.5
+
+
+@pytest.mark.parametrize("k", [3, 5, 7])
+def test_shared_block_conditions(api, k):
+    """Fragments where u + a rounds up to the next integer (u just below a
+    power of two minus a), and fragments at the map's borders, where the
+    samples' texels cannot come from one shared block: the same answers as
+    the oracle, and texture gathers equal to plain loads."""
+    w, h = 8192, 40
+    rng = np.random.default_rng(k)
+    depth = np.where(rng.random((h, w)) < 0.35, np.float32(0.25), np.float32(1.0)).astype(np.float32)
+    us = []
+    for b in (2048.0, 4096.0, 8192.0):
+        for a in range(0, 4):
+            for t in range(0, 6):
+                us.append(b - a - t * 2.0 ** -12)       # ulp of [2048, 4096) is 2^-12
+                us.append(b - a - t * 2.0 ** -11)
+    us += [0.0, 0.5, 1.0, 1.999, 2.0, 2.5, 3.0, 3.5, 4.0, 8188.5, 8189.0, 8190.25, 8191.75]
+    u = np.unique(np.array(us, np.float32).astype(np.float64))   # representable texel-space positions
+    u = u[(u >= 0) & (u < w)]
+    vv = rng.uniform(0, h, u.size * 8)
+    uu = np.repeat(u, 8)
+    x = (uu / w).astype(np.float32)
+    assert np.array_equal(x.astype(np.float64) * w, uu)   # u = x * 8192 exactly
+    y = (vv / h).astype(np.float32)
+    z = np.full_like(x, 0.5)
+    check(api, depth, x, y, z, k, "block k=%d" % k)
