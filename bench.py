@@ -275,6 +275,39 @@ def oracle_throughput(host_frames, min_seconds=10.0):
                       "both visibility functions, %.1f s" % (frames_done, len(host_frames), dt)}
 
 
+def edge_statistics(host_frames, per_frame=65536, max_dist=16, seed=11):
+    """The workload's edge-fragment fraction and traversal-length histogram
+    (reported next to the CPU baseline; untimed): the oracle's four walks of
+    the edge fragments of a uniform sample of every frame.  A walk's length
+    is |rd| texels (the fragment's texel included); `capped` counts walks
+    that reached max_dist without an end."""
+    import numpy as np
+    from oracle import rbsm as orc
+    rng = np.random.default_rng(seed)
+    edge = total = 0
+    found = np.zeros(max_dist + 2, np.int64)
+    open_ = np.zeros(max_dist + 2, np.int64)
+    for fr in host_frames:
+        xyz = fr["xyz"].numpy()
+        idx = np.sort(rng.choice(xyz.shape[1], min(per_frame, xyz.shape[1]), replace=False))
+        r = orc.evaluate(fr["depth"].numpy(), xyz[0, idx], xyz[1, idx], xyz[2, idx], orc.MODE_FILTER,
+                         max_dist=max_dist, want_rd=True)
+        walked = (r["codes"] & (1 << 9)) != 0
+        total += idx.size
+        edge += int(walked.sum())
+        rd = r["rd"][walked].ravel()
+        found += np.bincount(rd[rd > 0], minlength=max_dist + 2)[:max_dist + 2]
+        open_ += np.bincount(-rd[rd < 0], minlength=max_dist + 2)[:max_dist + 2]
+    return {"fraction": edge / max(total, 1), "sample_fragments": total,
+            "walk_length_histogram": {
+                "length": list(range(1, max_dist + 2)),
+                "end_found": found[1:].tolist(),
+                "no_end": open_[1:].tolist()},
+            "capped_walks": int(open_[max_dist + 1]),
+            "walks": int(found.sum() + open_.sum()),
+            "sample": "%d fragments per frame of every frame, oracle walks, max_dist %d" % (per_frame, max_dist)}
+
+
 # ------------------------------------------------------------------- ours --
 
 def run_ours(args, rank, world, local_rank):
@@ -409,8 +442,10 @@ def run_ours(args, rank, world, local_rank):
         learned = compare_learned(api, texs or maps, xyz, frames, n_frag, args, stream)
 
     cpu = None
+    edges = {}
     if rank == 0 and world == 1 and not args.skip_cpu:
         cpu = oracle_throughput(host)
+        edges = edge_statistics(host)
 
     line = {
         "metric": METRIC, "value": world * frames * n_frag / (ms_per_step * 1e-3) / 1e9, "unit": UNIT,
@@ -443,7 +478,7 @@ def run_ours(args, rank, world, local_rank):
         "frame_pipeline": light["frame_pipeline"] if light else None,
         "gpu_launches": args.steps,
         "clocks": clocks,
-        "edge": {"unique_texels_per_frame": statistics.mean(h["U"] for h in host)},
+        "edge": dict({"unique_texels_per_frame": statistics.mean(h["U"] for h in host)}, **edges),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

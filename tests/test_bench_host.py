@@ -65,3 +65,24 @@ def test_recorded_traffic_requires_matching_kernel_sources(tmp_path, monkeypatch
     assert bench.recorded_traffic(32) == pytest.approx(4.8e9)
     f.write_text("source_hash: 0000\ndram_bytes_per_frame: 1.5e8\n")
     assert bench.recorded_traffic(32) is None
+
+
+def test_edge_statistics_invariants():
+    """The edge statistics of the bench line: four walks per edge fragment,
+    every walk at most max_dist + 1 texels long, and only unfinished walks
+    may reach that length."""
+    import numpy as np
+    import torch
+    import bench
+    rng = np.random.default_rng(3)
+    depth = np.where(rng.random((64, 64)) < 0.3, np.float32(0.4), np.float32(1.0)).astype(np.float32)
+    xyz = np.stack([rng.random(5000), rng.random(5000), np.full(5000, 0.9)]).astype(np.float32)
+    host = [{"depth": torch.from_numpy(depth), "xyz": torch.from_numpy(xyz)}]
+    e = bench.edge_statistics(host, per_frame=4000, max_dist=8)
+    h = e["walk_length_histogram"]
+    assert h["length"] == list(range(1, 10))
+    assert e["sample_fragments"] == 4000
+    n_edge = round(e["fraction"] * 4000)
+    assert 0 < n_edge < 4000
+    assert e["walks"] == 4 * n_edge == sum(h["end_found"]) + sum(h["no_end"])
+    assert h["end_found"][-1] == 0 and e["capped_walks"] == h["no_end"][-1]
