@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "rbsm.h"
 #include "rbsm_device.cuh"
 
@@ -18,10 +20,11 @@ MapDev to_dev(const rbsm_map &m);
 
 // Per-device cache of "dynamic shared memory attribute set + occupancy" for
 // one kernel.  The attribute is a per-device property, so it is set once on
-// every device the kernel is launched on.
+// every device the kernel is launched on.  Host threads may race on the
+// first launch: each computes the same value, and the slots are atomics.
 struct KernelSetup {
     static constexpr int kMaxDevices = 64;
-    int occupancy[kMaxDevices] = {};
+    std::atomic<int> occupancy[kMaxDevices] = {};
 
     template <typename Kernel>
     int get(Kernel kern, int threads, size_t smem, int *occ)
@@ -32,7 +35,8 @@ struct KernelSetup {
             return cuda_fail(e);
         if (dev < 0 || dev >= kMaxDevices)
             return cuda_fail(cudaErrorInvalidDevice);
-        if (occupancy[dev] == 0) {
+        int known = occupancy[dev].load(std::memory_order_acquire);
+        if (known == 0) {
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess)
                 return cuda_fail(e);
@@ -42,9 +46,10 @@ struct KernelSetup {
                 return cuda_fail(e);
             if (o < 1)
                 return cuda_fail(cudaErrorInvalidConfiguration);
-            occupancy[dev] = o;
+            occupancy[dev].store(o, std::memory_order_release);
+            known = o;
         }
-        *occ = occupancy[dev];
+        *occ = known;
         return RBSM_OK;
     }
 };
