@@ -4,11 +4,11 @@
 // rectangles and sphere caps covering it.
 //
 // A CTA owns 32 x 32 texel tiles (persistent, grid-stride over tiles).  Per
-// tile it first culls the occluders, 256 at a time, with float tests that
-// can only keep too many (the tile's texel centres projected on the
+// tile it culls the occluders of both kinds, 256 at a time, with float tests
+// that can only keep too many (the tile's texel centres projected on the
 // rectangle's own two axes, the disc against the box of texel centres, both
-// widened by half a texel), gathers the survivors in shared memory, and then
-// every thread tests its 4 texels against them.  Double precision is slow on
+// widened by half a texel), gathers the survivors in shared memory in index
+// order, and every thread tests its 4 texels against them.  Double precision is slow on
 // this GPU, so the map's double-precision definition is reached mostly in
 // float:
 //   * the coverage tests run first in float, relative to the tile centre,
@@ -64,12 +64,18 @@ struct SphereCand {
     int fast;
 };
 
+// The survivors of one culling round (at most kChunk of both kinds): the
+// rectangles in index order from slot 0, then the spheres in index order.
+union Cand {
+    RectCand r;
+    SphereCand s;
+};
+
+constexpr int kSmWarps = kSmThreads / 32;
+
 struct TileSmem {
-    union {
-        RectCand r[kChunk];
-        SphereCand s[kChunk];
-    };
-    int n;
+    Cand c[kChunk];
+    int cnt_r[kSmWarps], cnt_s[kSmWarps];     // survivors per warp, for the order-keeping offsets
 };
 
 // Float copies of up to kFloatCopies occluders of each kind, made once per
@@ -256,83 +262,98 @@ __device__ __noinline__ float cap_depth_exact(const SphereCand &c, int i, int j,
     return __double2float_rn(__dsub_rn(c.c, drop));
 }
 
-// Cull occluders base + threadIdx.x against the tile centred at (tcx, tcy)
-// (float copies when the CTA holds them, else the double parameters) and
-// gather the survivors with their float pre-test data (and, for spheres
-// when `fast`, the float-float data of the cap depth).
-template <bool RECT, bool COPIES>
-__device__ __forceinline__ void cull_chunk(const rbsm_occluders &occ, const FloatOcc *fo, const FloatSph *fs,
-                                           int base, float tcx, float tcy, bool fast, TileSmem &sm)
+// Cull the occluders of combined index base + threadIdx.x (rectangles
+// 0..n_rects-1, then spheres) against the tile centred at (tcx, tcy) (float
+// copies when the CTA holds them, else the double parameters) and gather
+// the survivors with their float pre-test data (and, for spheres when
+// `fast`, the float-float data of the cap depth), each kind in index order
+// (ballots and per-warp counts, so every texel meets its occluders in the
+// definition's order).  nr, ns: the survivors of each kind.
+template <bool COPIES>
+__device__ __forceinline__ void cull_round(const rbsm_occluders &occ, const FloatOcc *fo, const FloatSph *fs,
+                                           long long base, float tcx, float tcy, bool fast, TileSmem &sm,
+                                           int &nr, int &ns)
 {
     constexpr float h = 0.5f * (kTile - 1);        // half size of the box of texel centres
-    const int k = base + (int)threadIdx.x;
-    const int n = RECT ? occ.n_rects : occ.n_spheres;
-    bool keep = false;
+    const long long g = base + (long long)threadIdx.x;
+    const unsigned lane = threadIdx.x & 31u;
+    const int warp = threadIdx.x >> 5;
+    bool keep_r = false, keep_s = false;
     RectCand rc;
     SphereCand sc;
-    if (k < n) {
-        if (RECT) {
-            const FloatOcc f = COPIES ? fo[k] : float_rect(occ.rects[k]);
-            // tcx - cx and the projections in float: the error is at most
-            // f.ea (centre rounding) + 2^-22 (|s0| + |t0|-size terms)
-            const float dx = tcx - f.cx, dy = tcy - f.cy;
-            rc.s0 = dx * f.ux + dy * f.uy;
-            rc.t0 = -dx * f.uy + dy * f.ux;
-            // |(q - tc) . u| over the tile's centres is at most h (|ux| + |uy|)
-            const float spread = h * (fabsf(f.ux) + fabsf(f.uy));
-            keep = fabsf(rc.s0) <= f.ha + spread + kCullSlack && fabsf(rc.t0) <= f.hb + spread + kCullSlack;
-            if (keep) {
-                const rbsm_rect r = occ.rects[k];
-                rc.uxf = f.ux;
-                rc.uyf = f.uy;
-                rc.haf = f.ha;
-                rc.hbf = f.hb;
-                const float mag = fabsf(dx) + fabsf(dy);
-                rc.es = err_bound(fabsf(rc.s0) + f.ha + spread + mag) + f.ea;
-                rc.et = err_bound(fabsf(rc.t0) + f.hb + spread + mag) + f.ea;
-                rc.cx = r.cx; rc.cy = r.cy; rc.ux = r.ux; rc.uy = r.uy; rc.ha = r.ha; rc.hb = r.hb;
-                rc.depth = r.depth;
-            }
-        } else {
-            const FloatSph f = COPIES ? fs[k] : float_sphere(occ.spheres[k], occ.zscale);
-            sc.dx0 = tcx - f.cx;
-            sc.dy0 = tcy - f.cy;
-            const float gx = fmaxf(fabsf(sc.dx0) - h, 0.0f), gy = fmaxf(fabsf(sc.dy0) - h, 0.0f);
-            const float rr = f.r + kCullSlack;
-            keep = gx * gx + gy * gy <= rr * rr;
-            if (keep) {
-                const rbsm_sphere c = occ.spheres[k];
-                sc.r2f = f.r * f.r;
-                const float far = fabsf(sc.dx0) + fabsf(sc.dy0) + 2.0f * h + f.r + f.ea;
-                sc.e = err_bound(far * far) + 2.0f * far * f.ea;
-                // the cap's depth is at least c - R / zscale (R widened by
-                // 1e-6 for the rounding of R^2 and the square root), one float below
-                sc.dmin = f.dmin;
-                sc.cx = c.cx; sc.cy = c.cy; sc.r = c.radius; sc.c = c.centre_depth;
-                // tile centre - disc centre in float-float: (tc - cx_f) exactly
-                // (TwoSum), then the dropped part of the centre
-                float a, e;
-                two_sum(tcx, -f.cx, a, e);
-                two_sum(a, __fsub_rn(e, f.cxl), sc.dx0h, sc.dx0l);
-                two_sum(tcy, -f.cy, a, e);
-                two_sum(a, __fsub_rn(e, f.cyl), sc.dy0h, sc.dy0l);
-                sc.r2h = f.r2h; sc.r2l = f.r2l; sc.ch = f.ch; sc.cl = f.cl;
-                sc.cxa = fabsf(f.cx);
-                sc.cya = fabsf(f.cy);
-                sc.fast = fast && f.fast && sc.cxa <= 1e15f && sc.cya <= 1e15f;
-            }
+    if (g < occ.n_rects) {
+        const int k = (int)g;
+        const FloatOcc f = COPIES ? fo[k] : float_rect(occ.rects[k]);
+        // tcx - cx and the projections in float: the error is at most
+        // f.ea (centre rounding) + 2^-22 (|s0| + |t0|-size terms)
+        const float dx = tcx - f.cx, dy = tcy - f.cy;
+        rc.s0 = dx * f.ux + dy * f.uy;
+        rc.t0 = -dx * f.uy + dy * f.ux;
+        // |(q - tc) . u| over the tile's centres is at most h (|ux| + |uy|)
+        const float spread = h * (fabsf(f.ux) + fabsf(f.uy));
+        keep_r = fabsf(rc.s0) <= f.ha + spread + kCullSlack && fabsf(rc.t0) <= f.hb + spread + kCullSlack;
+        if (keep_r) {
+            const rbsm_rect r = occ.rects[k];
+            rc.uxf = f.ux;
+            rc.uyf = f.uy;
+            rc.haf = f.ha;
+            rc.hbf = f.hb;
+            const float mag = fabsf(dx) + fabsf(dy);
+            rc.es = err_bound(fabsf(rc.s0) + f.ha + spread + mag) + f.ea;
+            rc.et = err_bound(fabsf(rc.t0) + f.hb + spread + mag) + f.ea;
+            rc.cx = r.cx; rc.cy = r.cy; rc.ux = r.ux; rc.uy = r.uy; rc.ha = r.ha; rc.hb = r.hb;
+            rc.depth = r.depth;
+        }
+    } else if (g - occ.n_rects < occ.n_spheres) {
+        const int k = (int)(g - occ.n_rects);
+        const FloatSph f = COPIES ? fs[k] : float_sphere(occ.spheres[k], occ.zscale);
+        sc.dx0 = tcx - f.cx;
+        sc.dy0 = tcy - f.cy;
+        const float gx = fmaxf(fabsf(sc.dx0) - h, 0.0f), gy = fmaxf(fabsf(sc.dy0) - h, 0.0f);
+        const float rr = f.r + kCullSlack;
+        keep_s = gx * gx + gy * gy <= rr * rr;
+        if (keep_s) {
+            const rbsm_sphere c = occ.spheres[k];
+            sc.r2f = f.r * f.r;
+            const float far = fabsf(sc.dx0) + fabsf(sc.dy0) + 2.0f * h + f.r + f.ea;
+            sc.e = err_bound(far * far) + 2.0f * far * f.ea;
+            sc.dmin = f.dmin;
+            sc.cx = c.cx; sc.cy = c.cy; sc.r = c.radius; sc.c = c.centre_depth;
+            // tile centre - disc centre in float-float: (tc - cx_f) exactly
+            // (TwoSum), then the dropped part of the centre
+            float a, e;
+            two_sum(tcx, -f.cx, a, e);
+            two_sum(a, __fsub_rn(e, f.cxl), sc.dx0h, sc.dx0l);
+            two_sum(tcy, -f.cy, a, e);
+            two_sum(a, __fsub_rn(e, f.cyl), sc.dy0h, sc.dy0l);
+            sc.r2h = f.r2h; sc.r2l = f.r2l; sc.ch = f.ch; sc.cl = f.cl;
+            sc.cxa = fabsf(f.cx);
+            sc.cya = fabsf(f.cy);
+            sc.fast = fast && f.fast && sc.cxa <= 1e15f && sc.cya <= 1e15f;
         }
     }
-    if (threadIdx.x == 0)
-        sm.n = 0;
-    __syncthreads();
-    if (keep) {
-        const int slot = atomicAdd(&sm.n, 1);
-        if (RECT)
-            sm.r[slot] = rc;
-        else
-            sm.s[slot] = sc;
+    const unsigned br = __ballot_sync(0xffffffffu, keep_r), bs = __ballot_sync(0xffffffffu, keep_s);
+    if (lane == 0) {
+        sm.cnt_r[warp] = __popc(br);
+        sm.cnt_s[warp] = __popc(bs);
     }
+    __syncthreads();
+    int off_r = 0, off_s = 0;
+    nr = 0;
+    ns = 0;
+#pragma unroll
+    for (int w = 0; w < kSmWarps; ++w) {
+        const int cr = sm.cnt_r[w], cs = sm.cnt_s[w];
+        off_r += w < warp ? cr : 0;
+        off_s += w < warp ? cs : 0;
+        nr += cr;
+        ns += cs;
+    }
+    const unsigned below = (1u << lane) - 1u;
+    if (keep_r)
+        sm.c[off_r + __popc(br & below)].r = rc;
+    if (keep_s)
+        sm.c[nr + off_s + __popc(bs & below)].s = sc;
     __syncthreads();
 }
 
@@ -361,8 +382,6 @@ __global__ void __launch_bounds__(kSmThreads) shadow_map_kernel(const rbsm_occlu
     // the float-float cap depth needs 1 / zscale exact in float
     const bool fast = inv_zscale >= 7.888609052210118e-31 && inv_zscale <= 1.2676506002282294e30;   // 2^-100, 2^100
     const float invf = (float)inv_zscale;
-    const int tiles_x = (width + kTile - 1) / kTile;
-    const int tiles = tiles_x * ((height + kTile - 1) / kTile);     // <= 2^22
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     constexpr float h = 0.5f * (kTile - 1);
     // texel centre - tile centre, exact: ox for this thread's column, oy[p]
@@ -372,15 +391,17 @@ __global__ void __launch_bounds__(kSmThreads) shadow_map_kernel(const rbsm_occlu
 #pragma unroll
     for (int p = 0; p < 4; ++p)
         oys[p] = __fsub_rn(small_int_float(ty + 8 * p), h);
+    const long long n_all = (long long)occ.n_rects + occ.n_spheres;
+    const long long pitch8 = pitch * 8;
     // the tile's column and row, stepped by the grid stride (no division per
-    // tile), and the offset of its first row in the map, stepped too: 64-bit
-    // integer multiplies share the slow FP64 pipe of this GPU
+    // tile), and the offset of this thread's first row in the map
+    const int tiles_x = (width + kTile - 1) / kTile;
+    const int tiles = tiles_x * ((height + kTile - 1) / kTile);     // <= 2^22
     int tcol = (int)blockIdx.x % tiles_x, trow = (int)blockIdx.x / tiles_x;
     const int step_col = (int)gridDim.x % tiles_x, step_row = (int)gridDim.x / tiles_x;
     const long long tile_rows = (long long)kTile * pitch;
     const long long step_rows = (long long)step_row * tile_rows;
-    long long row0 = (long long)trow * tile_rows + (long long)ty * pitch;   // this thread's first row
-    const long long pitch8 = pitch * 8;
+    long long row0 = (long long)trow * tile_rows + (long long)ty * pitch;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int i0 = tcol * kTile, j0 = trow * kTile;
         float *out = depth + row0 + i0 + tx;
@@ -399,10 +420,14 @@ __global__ void __launch_bounds__(kSmThreads) shadow_map_kernel(const rbsm_occlu
 #pragma unroll
         for (int p = 0; p < 4; ++p)
             best[p] = occ.ground;
-        for (int base = 0; base < occ.n_rects; base += kChunk) {
-            cull_chunk<true, COPIES>(occ, fop, fsp, base, tcx, tcy, false, sm);
-            for (int q = 0; q < sm.n; ++q) {
-                const RectCand &r = sm.r[q];
+        // occluders in rounds of kChunk: rectangles, then spheres, in index
+        // order (the next round's first barrier keeps its survivors from
+        // overwriting these before every warp has read them)
+        for (long long base = 0; base < n_all; base += kChunk) {
+            int nr, ns;
+            cull_round<COPIES>(occ, fop, fsp, base, tcx, tcy, fast, sm, nr, ns);
+            for (int q = 0; q < nr; ++q) {
+                const RectCand &r = sm.c[q].r;
                 const float sx = ox * r.uxf, tx_ = -ox * r.uyf;
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
@@ -418,12 +443,8 @@ __global__ void __launch_bounds__(kSmThreads) shadow_map_kernel(const rbsm_occlu
                         best[p] = r.depth;
                 }
             }
-            __syncthreads();                       // survivors read before the next chunk
-        }
-        for (int base = 0; base < occ.n_spheres; base += kChunk) {
-            cull_chunk<false, COPIES>(occ, fop, fsp, base, tcx, tcy, fast, sm);
-            for (int q = 0; q < sm.n; ++q) {
-                const SphereCand &c = sm.s[q];
+            for (int q = 0; q < ns; ++q) {
+                const SphereCand &c = sm.c[nr + q].s;
                 const float dxf = c.dx0 + ox;
                 const CapColumn col = cap_column(c, ox);
 #pragma unroll
@@ -442,7 +463,6 @@ __global__ void __launch_bounds__(kSmThreads) shadow_map_kernel(const rbsm_occlu
                         best[p] = d;
                 }
             }
-            __syncthreads();
         }
         if (i < width) {
 #pragma unroll
