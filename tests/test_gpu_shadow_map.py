@@ -136,3 +136,22 @@ def test_occluders_in_several_passes(api, nr, ns):
     got = gpu_map(api, rects, rdep, sph, w, h, 64.0, ground=0.99)
     assert same(got, ref)
     assert np.mean(ref < 0.99) > 0.5
+
+
+def test_signed_zero_ties_resolve_in_definition_order(api):
+    """Equal depths of different sign (+0, -0): a texel keeps the first in
+    the definition's order (rectangles by index, then spheres), which the
+    kernel's order-keeping gathering of survivors preserves."""
+    rng = np.random.default_rng(5)
+    n = 300
+    rects = np.stack([rng.uniform(0, 48, n), rng.uniform(0, 48, n), np.ones(n), np.zeros(n),
+                      rng.uniform(2, 10, n), rng.uniform(2, 10, n)], 1)
+    rdep = np.where(rng.random(n) < 0.5, np.float32(0.0), np.float32(-0.0)).astype(np.float32)
+    sph = np.stack([rng.uniform(0, 48, 40), rng.uniform(0, 48, 40), rng.uniform(1, 6, 40),
+                    rng.uniform(0, 6, 40) / 16.0], 1)
+    sph[:, 3] = sph[:, 2] / 16.0                   # caps reaching depth exactly 0 at their centres
+    ref = orc.shadow_map(48, 48, rects, rdep, sph, 16.0, ground=1.0)
+    got = gpu_map(api, rects, rdep, sph, 48, 48, 16.0, ground=1.0)
+    assert same(got, ref)
+    zero = ref == 0.0
+    assert np.any(zero & np.signbit(ref)) and np.any(zero & ~np.signbit(ref))
