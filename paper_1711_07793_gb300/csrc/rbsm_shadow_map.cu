@@ -128,8 +128,8 @@ __device__ __forceinline__ FloatSph float_sphere(const rbsm_sphere &c, double zs
     return f;
 }
 
-// n as a float for 0 <= n < 2^23, from the bit pattern of 2^23 + n (the
-// int-to-float conversion runs on the slow FP64 pipe of this GPU).
+// n as a float for 0 <= n < 2^23, from the bit pattern of 2^23 + n (an
+// exact conversion in two integer/float operations).
 __device__ __forceinline__ float small_int_float(int n)
 {
     return __fsub_rn(__int_as_float(0x4B000000 | n), 8388608.0f);
