@@ -4,8 +4,8 @@
  * and Aguero, "Optimized Visibility Functions for Revectorization-Based
  * Shadow Mapping" (TR-PGCOMP-007/2017).
  *
- * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct judge
- * of the CUDA path.  Only the tests, the smoke check and the benchmark's CPU
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * reference that the CUDA path is checked against.  Only the tests, the smoke check and the benchmark's CPU
  * baseline may load it.  It shares no code, header, table or helper with the
  * CUDA library, and it never reads a value the CUDA library produced.
  *

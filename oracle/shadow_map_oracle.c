@@ -5,7 +5,8 @@
  * the occluders are oriented rectangles and spheres seen by an
  * orthographic light looking down the depth axis).
  *
- * TEST INFRASTRUCTURE ONLY: the judge of the CUDA rasteriser.  Only the
+ * TEST INFRASTRUCTURE ONLY: the reference the CUDA rasteriser is checked
+ * against.  Only the
  * tests, the smoke check and the benchmark's CPU baseline may load it; it
  * shares no code with the CUDA library.
  *

@@ -377,8 +377,10 @@ __device__ __forceinline__ void resolve_edge(const MapDev &m, float x, float y, 
 // value) and appends its edge fragments to its own shared-memory queue.  The
 // queue is drained 32 entries at a time, so the walks run with all 32 lanes
 // busy, and the drained answers overwrite the provisional ones (still in L2).
-// While a warp works on one tile, the loads of its next tile's coordinates
-// are already in flight (register double buffering).
+// While a warp works on one tile, the copies of its next tile's coordinates
+// into the warp's shared-memory buffer are already in flight (cp.async;
+// `stage_tile` / `fetch_tile`; the depth-buffer kernel keeps its next tile's
+// depths in registers, a quarter of the bytes).
 
 constexpr int kWarpTile = 32 * kPerThread;   // 128 fragments
 constexpr int kQueueCap = kWarpTile + 32;    // < 32 left over + one tile

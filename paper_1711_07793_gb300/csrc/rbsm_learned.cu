@@ -4,7 +4,7 @@
 // an edge fragment from its 5x5 shadow-test pattern, in-texel offsets and
 // blocker-receiver depth gap.  Training data come from the plain RSMSS
 // (this library's exact walk), so the plain method is the surrogate's
-// teacher, its fallback and its judge.
+// teacher, its fallback and the measure of its error.
 //
 // The network state lives in one caller-allocated device block
 // (rbsm_mlp_state_bytes): FP32 master parameters, their gradient, the two
