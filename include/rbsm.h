@@ -229,7 +229,8 @@ typedef struct {
     /* Learned penumbra (not in the paper): NULL = exact everywhere.  Given a
      * network state block (rbsm_mlp_state_bytes), FILTER-mode jobs answer
      * their edge fragments with the surrogate wherever its own error
-     * estimate is <= guard_tau and fall back to the exact walk elsewhere;
+     * estimate is <= guard_tau (0 <= guard_tau < 1e30) and fall back to
+     * the exact walk elsewhere;
      * shadow tests, discontinuity codes and off-edge answers stay exact, and
      * SILHOUETTE / BOTH jobs are not touched.  A surrogate answer's code has
      * bit 10 set and no end counts (bits 5-9 clear). */
