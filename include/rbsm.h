@@ -150,7 +150,11 @@ int rsmss_filter(const rbsm_map *map, const rbsm_frags *frags, float *vis,
  * the answers are those of those calls on the projected planes, bit for
  * bit, and 4 bytes per fragment are read instead of 12.  Every job is
  * checked before the first launch; then each job runs as one launch, in
- * order, on `stream`.
+ * order, on `stream`.  When no job's outputs overlap another job's outputs
+ * or any job's inputs (depth buffer, map), each job after the first is a
+ * programmatic dependent launch: it takes SMs as the previous job's kernel
+ * drains instead of after it ends.  Work after the call on `stream` still
+ * follows all of them.
  *   jobs: n_jobs (1..RBSM_GBUFFER_MAX_JOBS) descriptors, copied into the
  *   launch; mode: RBSM_MODE_SILHOUETTE, _FILTER or _BOTH for every job;
  *   vis_silhouette / vis_filter: width * height floats each as the mode

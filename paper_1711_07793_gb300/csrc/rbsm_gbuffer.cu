@@ -60,6 +60,9 @@ gbuffer_kernel(const MapDev m, const GBufDev g, float *__restrict__ sil, float *
 {
     constexpr int kWarps = kThreads / 32;
     __shared__ WarpQueue wq[kWarps];
+    // the next job's kernel (launched as a programmatic dependent when the
+    // jobs share no output) may take SMs as this one's CTAs finish
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const unsigned lane = lane_id();
     const int warp = threadIdx.x >> 5;
     const long long n = (long long)g.width * g.height;
@@ -159,7 +162,7 @@ gbuffer_kernel(const MapDev m, const GBufDev g, float *__restrict__ sil, float *
 
 template <int MODE, bool CODES>
 int launch_gbuffer(const MapDev &map, const GBufDev &g, float *sil, float *fil, uint16_t *codes, bool vec,
-                   int max_dist, cudaStream_t stream)
+                   int max_dist, bool overlap, cudaStream_t stream)
 {
     constexpr int kThreads = 256;
     auto kern = gbuffer_kernel<MODE, CODES, kThreads>;
@@ -177,11 +180,78 @@ int launch_gbuffer(const MapDev &map, const GBufDev &g, float *sil, float *fil, 
     long long grid = (long long)sms * occupancy;
     if (grid > blocks_needed)
         grid = blocks_needed;
-    kern<<<(unsigned)grid, kThreads, 0, stream>>>(map, g, sil, fil, codes, max_dist, vec);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e;
+    if (overlap) {
+        // a programmatic dependent of the previous job's kernel: it starts as
+        // that kernel's CTAs finish instead of after its last one, and does
+        // not wait for it (the jobs share no output, and everything before
+        // the call is complete before the first job's kernel starts)
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, kern, map, g, sil, fil, codes, max_dist, vec);
+    } else {
+        kern<<<(unsigned)grid, kThreads, 0, stream>>>(map, g, sil, fil, codes, max_dist, vec);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess)
         return cuda_fail(e);
     return RBSM_OK;
+}
+
+struct Span {
+    uintptr_t lo, hi;    // [lo, hi) bytes
+};
+
+bool spans_meet(const Span &a, const Span &b) { return a.lo < b.hi && b.lo < a.hi; }
+
+// Whether the jobs' outputs are pairwise disjoint and disjoint from every
+// job's inputs (depth buffer, map), so that the jobs' kernels may overlap.
+bool jobs_independent(const rbsm_gbuffer_job *jobs, int n_jobs, int mode, bool codes)
+{
+    Span out[RBSM_GBUFFER_MAX_JOBS * 3], in[RBSM_GBUFFER_MAX_JOBS * 2];
+    int n_out = 0, n_in = 0, owner[RBSM_GBUFFER_MAX_JOBS * 3];
+    for (int k = 0; k < n_jobs; ++k) {
+        const rbsm_gbuffer_job &j = jobs[k];
+        const uintptr_t n = (uintptr_t)j.gbuffer.width * (uintptr_t)j.gbuffer.height;
+        const uintptr_t d = reinterpret_cast<uintptr_t>(j.gbuffer.depth);
+        in[n_in++] = Span{d, d + ((uintptr_t)j.gbuffer.pitch * (uintptr_t)(j.gbuffer.height - 1) +
+                                  (uintptr_t)j.gbuffer.width) * 4u};
+        const uintptr_t md = reinterpret_cast<uintptr_t>(j.map.depth);
+        in[n_in++] = Span{md, md + ((uintptr_t)j.map.pitch * (uintptr_t)(j.map.height - 1) +
+                                    (uintptr_t)j.map.width) * 4u};
+        if (mode & 1) {
+            const uintptr_t p = reinterpret_cast<uintptr_t>(j.vis_silhouette);
+            owner[n_out] = k;
+            out[n_out++] = Span{p, p + n * 4u};
+        }
+        if (mode & 2) {
+            const uintptr_t p = reinterpret_cast<uintptr_t>(j.vis_filter);
+            owner[n_out] = k;
+            out[n_out++] = Span{p, p + n * 4u};
+        }
+        if (codes) {
+            const uintptr_t p = reinterpret_cast<uintptr_t>(j.codes);
+            owner[n_out] = k;
+            out[n_out++] = Span{p, p + n * 2u};
+        }
+    }
+    for (int a = 0; a < n_out; ++a) {
+        for (int b = a + 1; b < n_out; ++b)
+            if (owner[a] != owner[b] && spans_meet(out[a], out[b]))
+                return false;
+        for (int b = 0; b < n_in; ++b)
+            if (spans_meet(out[a], in[b]))
+                return false;
+    }
+    return true;
 }
 
 }  // namespace
@@ -213,7 +283,9 @@ extern "C" int rbsm_visibility_gbuffer(const rbsm_gbuffer_job *jobs, int32_t n_j
             return RBSM_ERR_ARG;
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const bool independent = n_jobs > 1 && jobs_independent(jobs, n_jobs, mode, codes);
     for (int k = 0; k < n_jobs; ++k) {
+        const bool overlap = independent && k > 0;
         const rbsm_gbuffer_job &j = jobs[k];
         const rbsm_gbuffer &gb = j.gbuffer;
         GBufDev g;
@@ -232,16 +304,16 @@ extern "C" int rbsm_visibility_gbuffer(const rbsm_gbuffer_job *jobs, int32_t n_j
         const MapDev map = to_dev(j.map);
         switch (mode) {
         case RBSM_MODE_SILHOUETTE:
-            rc = codes ? launch_gbuffer<1, true>(map, g, sil, fil, j.codes, vec, max_dist, s)
-                       : launch_gbuffer<1, false>(map, g, sil, fil, nullptr, vec, max_dist, s);
+            rc = codes ? launch_gbuffer<1, true>(map, g, sil, fil, j.codes, vec, max_dist, overlap, s)
+                       : launch_gbuffer<1, false>(map, g, sil, fil, nullptr, vec, max_dist, overlap, s);
             break;
         case RBSM_MODE_FILTER:
-            rc = codes ? launch_gbuffer<2, true>(map, g, sil, fil, j.codes, vec, max_dist, s)
-                       : launch_gbuffer<2, false>(map, g, sil, fil, nullptr, vec, max_dist, s);
+            rc = codes ? launch_gbuffer<2, true>(map, g, sil, fil, j.codes, vec, max_dist, overlap, s)
+                       : launch_gbuffer<2, false>(map, g, sil, fil, nullptr, vec, max_dist, overlap, s);
             break;
         default:
-            rc = codes ? launch_gbuffer<3, true>(map, g, sil, fil, j.codes, vec, max_dist, s)
-                       : launch_gbuffer<3, false>(map, g, sil, fil, nullptr, vec, max_dist, s);
+            rc = codes ? launch_gbuffer<3, true>(map, g, sil, fil, j.codes, vec, max_dist, overlap, s)
+                       : launch_gbuffer<3, false>(map, g, sil, fil, nullptr, vec, max_dist, overlap, s);
         }
         if (rc != RBSM_OK)
             return rc;

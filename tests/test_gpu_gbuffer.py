@@ -136,6 +136,49 @@ def test_many_jobs_in_one_launch(api):
             assert torch.equal(u, v)
 
 
+def _job_set(api, rng, n, w=200, h=90, out=None):
+    jobs, singles = [], []
+    for k in range(n):
+        depth = dev(np.where(rng.random((64, 96)) < 0.3, np.float32(0.4), np.float32(1.0)).astype(np.float32))
+        m = np.array([[1.0 / w, 0.05 / h, 0, 0.01 * k], [0.03 / w, 1.0 / h, 0, 0.02],
+                      [0, 0, 1, 0], [0.2 / w, 0.1 / h, 0, 1]], np.float32)
+        gd = dev(rng.uniform(0.3, 1.1, (h, w)).astype(np.float32))
+        jobs.append(api.GBufferJob(depth, gd, m, mode=2, vis_filter=out))
+        singles.append(api.GBufferJob(depth, gd, m, mode=2))
+    return jobs, singles
+
+
+def test_jobs_sharing_an_output_run_in_order(api):
+    """Jobs that write the same answer plane are not overlapped: the plane
+    ends with the last job's answers, as launches in order leave it."""
+    rng = np.random.default_rng(8)
+    shared = torch.empty(200 * 90, dtype=torch.float32, device="cuda")
+    jobs, singles = _job_set(api, rng, 6, out=shared)
+    api.rbsm_visibility_gbuffer(jobs, mode=2)
+    api.rbsm_visibility_gbuffer([singles[-1]], mode=2)
+    torch.cuda.synchronize()
+    assert torch.equal(shared, singles[-1].vis_filter)
+
+
+def test_overlapped_jobs_are_complete_for_the_next_work_on_the_stream(api):
+    """Independent jobs run as programmatic dependents of each other; work
+    queued on the stream right after the call (no synchronisation between)
+    sees every job's answers."""
+    rng = np.random.default_rng(9)
+    jobs, singles = _job_set(api, rng, 16)
+    for s_ in singles:
+        api.rbsm_visibility_gbuffer([s_], mode=2)
+    torch.cuda.synchronize()
+    for j in jobs:
+        j.vis_filter.fill_(-7.0)
+    api.rbsm_visibility_gbuffer(jobs, mode=2)
+    sums = torch.stack([j.vis_filter.sum() for j in jobs])      # same stream, no sync before
+    torch.cuda.synchronize()
+    assert torch.equal(sums, torch.stack([s_.vis_filter.sum() for s_ in singles]))
+    for a, b in zip(jobs, singles):
+        assert torch.equal(a.vis_filter, b.vis_filter)
+
+
 def test_bad_arguments(api):
     from paper_1711_07793_gb300 import _native as N
     d = dev(np.ones((8, 8), np.float32))
