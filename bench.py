@@ -590,11 +590,12 @@ def measure_rpcf(api, maps, xyz, frames, n_frag, args, stream, k=3):
 
 
 def measure_light_pass(api, c5, maps, frames, n_frag, step_fn, stream):
-    """The light pass on the GPU (rbsm_shadow_map): the frames' 8192^2 maps
-    rasterised from their analytic occluders into the bench's own map
-    buffers (the kernel writes the generator's bytes, checked here on one
-    frame), alone and followed by the visibility step: the per-frame
-    pipeline with maps made on the device."""
+    """The light pass on the GPU (rbsm_shadow_maps, one call for the
+    frames): the frames' 8192^2 maps rasterised from their analytic
+    occluders into the bench's own map buffers (the kernel writes the
+    generator's bytes, checked here on one frame with rbsm_shadow_map),
+    alone and followed by the visibility step: the per-frame pipeline with
+    maps made on the device."""
     import torch
     occs = [api.DeviceOccluders(o.rects, o.rect_depth, o.spheres)
             for o in (c5.occluders(f) for f in range(frames))]
@@ -605,8 +606,7 @@ def measure_light_pass(api, c5, maps, frames, n_frag, step_fn, stream):
     steps = 5
 
     def light():
-        for f in range(frames):
-            api.rbsm_shadow_map(occs[f], size, size, float(size), out=maps[f])
+        api.rbsm_shadow_maps(occs, size, size, float(size), outs=maps)
 
     def pipeline():
         light()
@@ -626,7 +626,7 @@ def measure_light_pass(api, c5, maps, frames, n_frag, step_fn, stream):
     ms_light = timed(light)
     ms_pipe = timed(pipeline)
     texels = frames * size * size
-    return {"light_pass": {"metric": "Gtexels/s shadow maps from analytic occluders (rbsm_shadow_map)",
+    return {"light_pass": {"metric": "Gtexels/s shadow maps from analytic occluders (rbsm_shadow_maps)",
                            "value": texels / (ms_light * 1e-3) / 1e9, "ms_per_step": ms_light, "maps": frames,
                            "map": size, "occluders_per_map": len(c5.base.rects) + len(c5.base.spheres),
                            "bytes_equal_to_generator": same,

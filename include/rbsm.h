@@ -384,6 +384,23 @@ int rbsm_shadow_map(const rbsm_occluders *occ, float *depth, int32_t width, int3
                     void *stream);
 
 /*
+ * n_maps (1..RBSM_SHADOW_MAPS_MAX) shadow maps of the same size and pitch in
+ * one call: map k from occluder set occ[k] (a host array of n_maps
+ * descriptors) into depth[k] (a host array of n_maps device pointers), each
+ * exactly as rbsm_shadow_map writes it, one launch per map, in order on
+ * `stream`.  When no map's memory meets another map's or any occluder
+ * array, each map after the first is a programmatic dependent launch that
+ * takes SMs as the previous map's kernel drains; work after the call on
+ * `stream` still follows all of them.  Every argument is checked before
+ * the first launch.
+ * Errors: RBSM_ERR_ARG as rbsm_shadow_map for any map, NULL arrays, or
+ * n_maps outside 1..RBSM_SHADOW_MAPS_MAX; RBSM_ERR_CUDA when a launch fails.
+ */
+#define RBSM_SHADOW_MAPS_MAX 256
+int rbsm_shadow_maps(const rbsm_occluders *occ, float *const *depth, int32_t n_maps, int32_t width,
+                     int32_t height, int64_t pitch, void *stream);
+
+/*
  * Host-resident batches: the stager (this library's addition; the paper
  * evaluates fragments where the renderer produced them, on the GPU, and has
  * no host-side interface).

@@ -95,6 +95,7 @@ class rbsm_gbuffer_job(ctypes.Structure):
 
 
 RBSM_GBUFFER_MAX_JOBS = 64
+RBSM_SHADOW_MAPS_MAX = 256
 
 
 class RBSMError(RuntimeError):
@@ -121,6 +122,9 @@ def _declare(lib):
     lib.rbsm_rpcf.argtypes = [_P(rbsm_map), _P(rbsm_frags), vp, ctypes.c_int32, _P(rbsm_params), vp]
     lib.rbsm_shadow_map.restype = i32
     lib.rbsm_shadow_map.argtypes = [_P(rbsm_occluders), vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, vp]
+    lib.rbsm_shadow_maps.restype = i32
+    lib.rbsm_shadow_maps.argtypes = [_P(rbsm_occluders), _P(vp), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_int64, vp]
     lib.rbsm_visibility_gbuffer.restype = i32
     lib.rbsm_visibility_gbuffer.argtypes = [_P(rbsm_gbuffer_job), ctypes.c_int32, ctypes.c_int32,
                                             _P(rbsm_params), vp]

@@ -438,6 +438,28 @@ def rbsm_shadow_map(occ, width, height, zscale, ground=1.0, out=None, stream=Non
     return out
 
 
+def rbsm_shadow_maps(occs, width, height, zscale, ground=1.0, outs=None, stream=None):
+    """Shadow maps of several DeviceOccluders sets in one call
+    (rbsm_shadow_maps): a list of (height, width) float32 CUDA tensors, or
+    `outs` (rows contiguous, one pitch for all); the maps' kernels overlap
+    when their memory is disjoint."""
+    occs = list(occs)
+    if outs is None:
+        outs = [torch.empty((int(height), int(width)), dtype=torch.float32, device=o.rects.device) for o in occs]
+    outs = list(outs)
+    if len(outs) != len(occs) or not outs:
+        raise ValueError("one output per occluder set")
+    for out in outs:
+        if (not out.is_cuda or out.dtype != torch.float32 or out.dim() != 2 or out.stride(1) != 1
+                or tuple(out.shape) != (int(height), int(width)) or out.stride(0) != outs[0].stride(0)):
+            raise ValueError("outs must be (height, width) float32 CUDA tensors with contiguous rows, one pitch")
+    descs = (N.rbsm_occluders * len(occs))(*[o.desc(zscale, ground) for o in occs])
+    ptrs = (ctypes.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+    N.check("rbsm_shadow_maps", N.lib().rbsm_shadow_maps(descs, ptrs, len(occs), int(width), int(height),
+                                                         outs[0].stride(0), _stream_handle(stream)))
+    return outs
+
+
 class GBufferJob:
     """One (shadow map, depth buffer) pair of rbsm_visibility_gbuffer: `depth`
     a map tensor or MapTexture, `gdepth` a (height, width) float32 CUDA

@@ -367,6 +367,9 @@ __global__ void __launch_bounds__(kSmThreads) shadow_map_kernel(const rbsm_occlu
                                                                 int width, int height, long long pitch,
                                                                 double inv_zscale)
 {
+    // the next map's kernel (a programmatic dependent when the maps share no
+    // memory) may take SMs as this one's CTAs finish
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __shared__ TileSmem sm;
     __shared__ FloatOcc fo[COPIES ? kFloatCopies : 1];
     __shared__ FloatSph fs[COPIES ? kFloatCopies : 1];
@@ -475,18 +478,18 @@ __global__ void __launch_bounds__(kSmThreads) shadow_map_kernel(const rbsm_occlu
     }
 }
 
-}  // namespace
-}  // namespace rbsm
-
-extern "C" int rbsm_shadow_map(const rbsm_occluders *occ, float *depth, int32_t width, int32_t height,
-                               int64_t pitch, void *stream)
+bool occluders_ok(const rbsm_occluders *occ)
 {
-    using namespace rbsm;
-    if (!occ || !depth || width < 1 || width > RBSM_MAX_EXTENT || height < 1 || height > RBSM_MAX_EXTENT ||
-        pitch < width || occ->n_rects < 0 || occ->n_spheres < 0 || (occ->n_rects > 0 && !occ->rects) ||
-        (occ->n_spheres > 0 && !occ->spheres) || !(occ->zscale > 0.0) || occ->flags != 0)
-        return RBSM_ERR_ARG;
-    const bool copies = occ->n_rects <= kFloatCopies && occ->n_spheres <= kFloatCopies;
+    return occ && occ->n_rects >= 0 && occ->n_spheres >= 0 && (occ->n_rects == 0 || occ->rects) &&
+           (occ->n_spheres == 0 || occ->spheres) && occ->zscale > 0.0 && occ->flags == 0;
+}
+
+// One map's launch; `overlap`: a programmatic dependent of the previous
+// kernel on the stream (it does not wait for it).
+int launch_map(const rbsm_occluders &occ, float *depth, int width, int height, long long pitch, bool overlap,
+               cudaStream_t stream)
+{
+    const bool copies = occ.n_rects <= kFloatCopies && occ.n_spheres <= kFloatCopies;
     static KernelSetup setup_copies, setup_plain;
     auto kern = copies ? shadow_map_kernel<true> : shadow_map_kernel<false>;
     int occupancy = 0;
@@ -501,11 +504,81 @@ extern "C" int rbsm_shadow_map(const rbsm_occluders *occ, float *depth, int32_t 
     if (grid > tiles)
         grid = tiles;
     int e2 = 0;
-    const double inv = std::frexp(occ->zscale, &e2) == 0.5 ? std::ldexp(1.0, 1 - e2) : 0.0;
-    kern<<<(unsigned)grid, kSmThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(*occ, depth, width, height,
-                                                                                   pitch, inv);
-    cudaError_t e = cudaGetLastError();
+    const double inv = std::frexp(occ.zscale, &e2) == 0.5 ? std::ldexp(1.0, 1 - e2) : 0.0;
+    cudaError_t e;
+    if (overlap) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.blockDim = dim3(kSmThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, kern, occ, depth, width, height, pitch, inv);
+    } else {
+        kern<<<(unsigned)grid, kSmThreads, 0, stream>>>(occ, depth, width, height, pitch, inv);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess)
         return cuda_fail(e);
+    return RBSM_OK;
+}
+
+bool spans_meet(uintptr_t a_lo, uintptr_t a_hi, uintptr_t b_lo, uintptr_t b_hi)
+{
+    return a_lo < b_hi && b_lo < a_hi;
+}
+
+}  // namespace
+}  // namespace rbsm
+
+extern "C" int rbsm_shadow_map(const rbsm_occluders *occ, float *depth, int32_t width, int32_t height,
+                               int64_t pitch, void *stream)
+{
+    using namespace rbsm;
+    if (!occluders_ok(occ) || !depth || width < 1 || width > RBSM_MAX_EXTENT || height < 1 ||
+        height > RBSM_MAX_EXTENT || pitch < width)
+        return RBSM_ERR_ARG;
+    return launch_map(*occ, depth, width, height, pitch, false, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int rbsm_shadow_maps(const rbsm_occluders *occ, float *const *depth, int32_t n_maps, int32_t width,
+                                int32_t height, int64_t pitch, void *stream)
+{
+    using namespace rbsm;
+    if (!occ || !depth || n_maps < 1 || n_maps > RBSM_SHADOW_MAPS_MAX || width < 1 || width > RBSM_MAX_EXTENT ||
+        height < 1 || height > RBSM_MAX_EXTENT || pitch < width)
+        return RBSM_ERR_ARG;
+    for (int k = 0; k < n_maps; ++k)
+        if (!occluders_ok(occ + k) || !depth[k])
+            return RBSM_ERR_ARG;
+    // the maps' kernels may overlap when no map's memory meets another map's
+    // or any occluder array
+    const uintptr_t map_bytes = ((uintptr_t)pitch * (uintptr_t)(height - 1) + (uintptr_t)width) * sizeof(float);
+    bool independent = n_maps > 1;
+    for (int a = 0; a < n_maps && independent; ++a) {
+        const uintptr_t lo = reinterpret_cast<uintptr_t>(depth[a]), hi = lo + map_bytes;
+        for (int b = 0; b < n_maps && independent; ++b) {
+            const uintptr_t blo = reinterpret_cast<uintptr_t>(depth[b]);
+            if (b != a && spans_meet(lo, hi, blo, blo + map_bytes))
+                independent = false;
+            const uintptr_t r = reinterpret_cast<uintptr_t>(occ[b].rects);
+            const uintptr_t sp = reinterpret_cast<uintptr_t>(occ[b].spheres);
+            if (occ[b].n_rects > 0 && spans_meet(lo, hi, r, r + (uintptr_t)occ[b].n_rects * sizeof(rbsm_rect)))
+                independent = false;
+            if (occ[b].n_spheres > 0 &&
+                spans_meet(lo, hi, sp, sp + (uintptr_t)occ[b].n_spheres * sizeof(rbsm_sphere)))
+                independent = false;
+        }
+    }
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    for (int k = 0; k < n_maps; ++k) {
+        const int rc = launch_map(occ[k], depth[k], width, height, pitch, independent && k > 0, s);
+        if (rc != RBSM_OK)
+            return rc;
+    }
     return RBSM_OK;
 }

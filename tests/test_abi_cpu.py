@@ -156,6 +156,16 @@ def test_bad_arguments_are_rejected_before_any_cuda_call(native):
     for bad in (N.rbsm_occluders(None, 1, None, 0, 1.0, 1.0, 0), N.rbsm_occluders(None, 0, None, -1, 1.0, 1.0, 0),
                 N.rbsm_occluders(None, 0, None, 0, 0.0, 1.0, 0), N.rbsm_occluders(None, 0, None, 0, 1.0, 1.0, 2)):
         assert lib.rbsm_shadow_map(B(bad), addr, 4, 4, 4, None) == N.RBSM_ERR_ARG
+    occs = (N.rbsm_occluders * 2)(occ, occ)
+    ptrs = (ctypes.c_void_p * 2)(addr, addr + 4096)
+    assert lib.rbsm_shadow_maps(None, ptrs, 2, 4, 4, 4, None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_shadow_maps(occs, None, 2, 4, 4, 4, None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_shadow_maps(occs, ptrs, 0, 4, 4, 4, None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_shadow_maps(occs, ptrs, N.RBSM_SHADOW_MAPS_MAX + 1, 4, 4, 4, None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_shadow_maps(occs, ptrs, 2, 4, 4, 3, None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_shadow_maps(occs, (ctypes.c_void_p * 2)(addr, None), 2, 4, 4, 4, None) == N.RBSM_ERR_ARG
+    bad2 = (N.rbsm_occluders * 2)(occ, N.rbsm_occluders(None, 1, None, 0, 1.0, 1.0, 0))
+    assert lib.rbsm_shadow_maps(bad2, ptrs, 2, 4, 4, 4, None) == N.RBSM_ERR_ARG
     assert lib.rbsm_status_string(N.RBSM_ERR_ARG) == b"invalid argument"
     assert lib.rbsm_version() >= 100
 

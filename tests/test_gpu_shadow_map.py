@@ -155,3 +155,26 @@ def test_signed_zero_ties_resolve_in_definition_order(api):
     assert same(got, ref)
     zero = ref == 0.0
     assert np.any(zero & np.signbit(ref)) and np.any(zero & ~np.signbit(ref))
+
+
+def test_several_maps_in_one_call(api):
+    """rbsm_shadow_maps: each map equals rbsm_shadow_map's bit for bit, with
+    the maps' kernels overlapped (separate buffers) and in order (one buffer
+    for all: it ends with the last map); work queued right after the call
+    sees every map."""
+    import rbsm_scenes as sc
+    c5 = sc.Config5(0, size=1024, frames=6)
+    occs = [api.DeviceOccluders(o.rects, o.rect_depth, o.spheres) for o in (c5.occluders(f) for f in range(6))]
+    singles = [api.rbsm_shadow_map(o, 1024, 1024, 1024.0) for o in occs]
+    torch.cuda.synchronize()
+    outs = [torch.full((1024, 1024), 7.0, device="cuda") for _ in occs]
+    api.rbsm_shadow_maps(occs, 1024, 1024, 1024.0, outs=outs)
+    sums = torch.stack([o.double().sum() for o in outs])          # same stream, no sync before
+    torch.cuda.synchronize()
+    assert torch.equal(sums, torch.stack([m.double().sum() for m in singles]))
+    for a, b in zip(outs, singles):
+        assert same(a.cpu().numpy(), b.cpu().numpy())
+    shared = torch.empty((1024, 1024), device="cuda")
+    api.rbsm_shadow_maps(occs, 1024, 1024, 1024.0, outs=[shared] * len(occs))
+    torch.cuda.synchronize()
+    assert same(shared.cpu().numpy(), singles[-1].cpu().numpy())
