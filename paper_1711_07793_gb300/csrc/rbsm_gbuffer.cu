@@ -26,9 +26,15 @@ struct GBufDev {
 
 // p of pixel (px, py) with depth d: M (px + 0.5, py + 0.5, d, 1), each row
 // summed left to right, then the perspective divide (all float32).
+// px as a float for 0 <= px < 2^23, from the bit pattern of 2^23 + px.
+__device__ __forceinline__ float pixel_float(int px)
+{
+    return __fsub_rn(__int_as_float(0x4B000000 | px), 8388608.0f);
+}
+
 __device__ __forceinline__ void project(const float (&m)[16], int px, int py, float d, float &x, float &y, float &z)
 {
-    const float sx = __fadd_rn((float)px, 0.5f), sy = __fadd_rn((float)py, 0.5f);
+    const float sx = __fadd_rn(pixel_float(px), 0.5f), sy = __fadd_rn(pixel_float(py), 0.5f);
     float v[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
@@ -137,14 +143,27 @@ gbuffer_kernel(const MapDev m, const GBufDev g, float *__restrict__ sil, float *
             load(tn, dn);                  // next tile's loads fly during this tile
         }
         LaneCoords c;
+        // the vector path's 4 fragments are consecutive pixels: one division
+        // for the first, then steps along the row (one wrap at most when the
+        // buffer is at least 4 pixels wide)
+        const bool steps = t.vec && g.width >= kPerThread;
+        int px = 0, py = 0;
+        if (steps)
+            pixel_of(g, t.first + 4 * (long long)lane, px, py);
 #pragma unroll
         for (int e = 0; e < kPerThread; ++e) {
             const long long f = t.first + (t.vec ? 4 * (long long)lane + e : (long long)lane + 32 * e);
             c.x[e] = c.y[e] = c.z[e] = 0.0f;
-            if (f < n) {
-                int px, py;
-                pixel_of(g, f, px, py);
+            if (steps) {
+                if (e > 0 && ++px == g.width) {
+                    px = 0;
+                    ++py;
+                }
                 project(g.m, px, py, d[e], c.x[e], c.y[e], c.z[e]);
+            } else if (f < n) {
+                int qx, qy;
+                pixel_of(g, f, qx, qy);
+                project(g.m, qx, qy, d[e], c.x[e], c.y[e], c.z[e]);
             }
         }
         classify_warp_tile<MODE, CODES>(m, t, c, wq[warp], queued);
