@@ -154,7 +154,9 @@ int rsmss_filter(const rbsm_map *map, const rbsm_frags *frags, float *vis,
  * or any job's inputs (depth buffer, map), each job after the first is a
  * programmatic dependent launch: it takes SMs as the previous job's kernel
  * drains instead of after it ends.  Work after the call on `stream` still
- * follows all of them.
+ * follows all of them.  The kernels signal their dependents at their
+ * start, so a caller's own programmatic dependent of this call must wait
+ * for it (cudaGridDependencySynchronize) before reading its outputs.
  *   jobs: n_jobs (1..RBSM_GBUFFER_MAX_JOBS) descriptors, copied into the
  *   launch; mode: RBSM_MODE_SILHOUETTE, _FILTER or _BOTH for every job;
  *   vis_silhouette / vis_filter: width * height floats each as the mode
@@ -391,8 +393,10 @@ int rbsm_shadow_map(const rbsm_occluders *occ, float *depth, int32_t width, int3
  * `stream`.  When no map's memory meets another map's or any occluder
  * array, each map after the first is a programmatic dependent launch that
  * takes SMs as the previous map's kernel drains; work after the call on
- * `stream` still follows all of them.  Every argument is checked before
- * the first launch.
+ * `stream` still follows all of them.  The kernels (of both calls) signal
+ * their dependents at their start, so a caller's own programmatic
+ * dependent must wait for them (cudaGridDependencySynchronize) before
+ * reading the maps.  Every argument is checked before the first launch.
  * Errors: RBSM_ERR_ARG as rbsm_shadow_map for any map, NULL arrays, or
  * n_maps outside 1..RBSM_SHADOW_MAPS_MAX; RBSM_ERR_CUDA when a launch fails.
  */
