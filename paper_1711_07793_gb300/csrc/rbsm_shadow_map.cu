@@ -46,13 +46,12 @@ constexpr float kCullSlack = 0.5f;        // texels added to every (float) culli
 // tile centre in float and an error bound E for the float pre-test: every
 // float decision further than E from its threshold is the exact one.
 struct RectCand {
-    double cx, cy, ux, uy, ha, hb;
     float s0, t0, uxf, uyf, haf, hbf, es, et;   // s, t at the tile centre; bounds of the float s, t
     float depth;
+    int k;                                        // the rectangle (its double parameters for the exact test)
 };
 
 struct SphereCand {
-    double cx, cy, r, c;
     float dx0, dy0, r2f, e;                       // centre offset from the tile centre; rho^2 bound
     float dmin;                                   // no texel of the cap is nearer the light than this
     // float-float data of the cap depth: tile centre - disc centre
@@ -62,6 +61,7 @@ struct SphereCand {
     // double operations
     float dx0h, dx0l, dy0h, dy0l, r2h, r2l, ch, cl, cxa, cya;
     int fast;
+    int k;                                        // the sphere (its double parameters for the exact depth)
 };
 
 // The survivors of one culling round (at most kChunk of both kinds): the
@@ -73,8 +73,13 @@ union Cand {
 
 constexpr int kSmWarps = kSmThreads / 32;
 
+// Each thread writes its survivor to its own slot of the round's buffer
+// (two buffers, alternating by round, so that a warp starting the next
+// round never overwrites candidates another warp still reads); the
+// order-keeping compaction moves only indices.
 struct TileSmem {
-    Cand c[kChunk];
+    Cand c[2][kChunk];
+    int idx[kChunk];                          // survivors' slots: rectangles, then spheres, in index order
     int cnt_r[kSmWarps], cnt_s[kSmWarps];     // survivors per warp, for the order-keeping offsets
 };
 
@@ -82,9 +87,9 @@ struct TileSmem {
 // CTA, for the culling and the float pre-tests; `ea` bounds what the
 // rounding of the centre to float moves any projection (|c - c_f| (|ux| +
 // |uy|) <= (|cx| + |cy|) 2^-24 * sqrt 2, taken as 2^-22).
-constexpr int kFloatCopies = 512;
+constexpr int kFloatCopies = 384;
 struct FloatOcc {
-    float cx, cy, ux, uy, ha, hb, ea;
+    float cx, cy, ux, uy, ha, hb, ea, depth;
 };
 struct FloatSph {
     float cx, cy, r, ea;         // cx, cy: the centre rounded to float
@@ -105,7 +110,8 @@ __device__ __forceinline__ float err_bound(float mag)
 __device__ __forceinline__ FloatOcc float_rect(const rbsm_rect &r)
 {
     return FloatOcc{(float)r.cx, (float)r.cy, (float)r.ux, (float)r.uy, (float)r.ha, (float)r.hb,
-                    (float)(fabs(r.cx) + fabs(r.cy)) * 2.384185791015625e-07f};    // 2^-22
+                    (float)(fabs(r.cx) + fabs(r.cy)) * 2.384185791015625e-07f,    // 2^-22
+                    r.depth};
 }
 
 __device__ __forceinline__ FloatSph float_sphere(const rbsm_sphere &c, double zscale)
@@ -240,8 +246,9 @@ __device__ __forceinline__ int cap_fast(const SphereCand &c, const CapColumn &k,
 // double operations in the defined order, without contraction.  Kept out
 // of the tile loop so that it holds no double values (their conversions and
 // arithmetic run on the slow FP64 pipe) for the few texels that need them.
-__device__ __noinline__ bool rect_covers_exact(const RectCand &r, int i, int j)
+__device__ __noinline__ bool rect_covers_exact(const rbsm_rect *rp, int i, int j)
 {
+    const rbsm_rect r = *rp;
     const double px = __dsub_rn((double)i + 0.5, r.cx), py = __dsub_rn((double)j + 0.5, r.cy);
     const double s = __dadd_rn(__dmul_rn(px, r.ux), __dmul_rn(py, r.uy));
     const double t = __dadd_rn(__dmul_rn(-px, r.uy), __dmul_rn(py, r.ux));
@@ -250,16 +257,17 @@ __device__ __noinline__ bool rect_covers_exact(const RectCand &r, int i, int j)
 
 // The cap depth of texel (i, j), or +infinity when the disc does not cover
 // it (a value that lowers no depth, as an uncovered texel).
-__device__ __noinline__ float cap_depth_exact(const SphereCand &c, int i, int j, double inv_zscale, double zscale)
+__device__ __noinline__ float cap_depth_exact(const rbsm_sphere *cp, int i, int j, double inv_zscale, double zscale)
 {
+    const rbsm_sphere c = *cp;
     const double dx = __dsub_rn((double)i + 0.5, c.cx), dy = __dsub_rn((double)j + 0.5, c.cy);
-    const double r2 = __dmul_rn(c.r, c.r);
+    const double r2 = __dmul_rn(c.radius, c.radius);
     const double rho2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
     if (rho2 > r2)
         return INFINITY;
     const double root = __dsqrt_rn(__dsub_rn(r2, rho2));
     const double drop = inv_zscale != 0.0 ? __dmul_rn(root, inv_zscale) : __ddiv_rn(root, zscale);
-    return __double2float_rn(__dsub_rn(c.c, drop));
+    return __double2float_rn(__dsub_rn(c.centre_depth, drop));
 }
 
 // Cull the occluders of combined index base + threadIdx.x (rectangles
@@ -272,7 +280,7 @@ __device__ __noinline__ float cap_depth_exact(const SphereCand &c, int i, int j,
 template <bool COPIES>
 __device__ __forceinline__ void cull_round(const rbsm_occluders &occ, const FloatOcc *fo, const FloatSph *fs,
                                            long long base, float tcx, float tcy, bool fast, TileSmem &sm,
-                                           int &nr, int &ns)
+                                           Cand *buf, int &nr, int &ns)
 {
     constexpr float h = 0.5f * (kTile - 1);        // half size of the box of texel centres
     const long long g = base + (long long)threadIdx.x;
@@ -293,7 +301,6 @@ __device__ __forceinline__ void cull_round(const rbsm_occluders &occ, const Floa
         const float spread = h * (fabsf(f.ux) + fabsf(f.uy));
         keep_r = fabsf(rc.s0) <= f.ha + spread + kCullSlack && fabsf(rc.t0) <= f.hb + spread + kCullSlack;
         if (keep_r) {
-            const rbsm_rect r = occ.rects[k];
             rc.uxf = f.ux;
             rc.uyf = f.uy;
             rc.haf = f.ha;
@@ -301,8 +308,9 @@ __device__ __forceinline__ void cull_round(const rbsm_occluders &occ, const Floa
             const float mag = fabsf(dx) + fabsf(dy);
             rc.es = err_bound(fabsf(rc.s0) + f.ha + spread + mag) + f.ea;
             rc.et = err_bound(fabsf(rc.t0) + f.hb + spread + mag) + f.ea;
-            rc.cx = r.cx; rc.cy = r.cy; rc.ux = r.ux; rc.uy = r.uy; rc.ha = r.ha; rc.hb = r.hb;
-            rc.depth = r.depth;
+            rc.depth = f.depth;
+            rc.k = k;
+            buf[threadIdx.x].r = rc;
         }
     } else if (g - occ.n_rects < occ.n_spheres) {
         const int k = (int)(g - occ.n_rects);
@@ -313,12 +321,11 @@ __device__ __forceinline__ void cull_round(const rbsm_occluders &occ, const Floa
         const float rr = f.r + kCullSlack;
         keep_s = gx * gx + gy * gy <= rr * rr;
         if (keep_s) {
-            const rbsm_sphere c = occ.spheres[k];
             sc.r2f = f.r * f.r;
             const float far = fabsf(sc.dx0) + fabsf(sc.dy0) + 2.0f * h + f.r + f.ea;
             sc.e = err_bound(far * far) + 2.0f * far * f.ea;
             sc.dmin = f.dmin;
-            sc.cx = c.cx; sc.cy = c.cy; sc.r = c.radius; sc.c = c.centre_depth;
+            sc.k = k;
             // tile centre - disc centre in float-float: (tc - cx_f) exactly
             // (TwoSum), then the dropped part of the centre
             float a, e;
@@ -330,6 +337,7 @@ __device__ __forceinline__ void cull_round(const rbsm_occluders &occ, const Floa
             sc.cxa = fabsf(f.cx);
             sc.cya = fabsf(f.cy);
             sc.fast = fast && f.fast && sc.cxa <= 1e15f && sc.cya <= 1e15f;
+            buf[threadIdx.x].s = sc;
         }
     }
     const unsigned br = __ballot_sync(0xffffffffu, keep_r), bs = __ballot_sync(0xffffffffu, keep_s);
@@ -351,9 +359,9 @@ __device__ __forceinline__ void cull_round(const rbsm_occluders &occ, const Floa
     }
     const unsigned below = (1u << lane) - 1u;
     if (keep_r)
-        sm.c[off_r + __popc(br & below)].r = rc;
+        sm.idx[off_r + __popc(br & below)] = (int)threadIdx.x;
     if (keep_s)
-        sm.c[nr + off_s + __popc(bs & below)].s = sc;
+        sm.idx[nr + off_s + __popc(bs & below)] = (int)threadIdx.x;
     __syncthreads();
 }
 
@@ -363,7 +371,7 @@ __device__ __forceinline__ void cull_round(const rbsm_occluders &occ, const Floa
 // kFloatCopies); a compile-time choice, so that the culling holds no
 // double-to-float conversions (slow FP64 pipe) when it reads the copies.
 template <bool COPIES>
-__global__ void __launch_bounds__(kSmThreads) shadow_map_kernel(const rbsm_occluders occ, float *__restrict__ depth,
+__global__ void __launch_bounds__(kSmThreads, 3) shadow_map_kernel(const rbsm_occluders occ, float *__restrict__ depth,
                                                                 int width, int height, long long pitch,
                                                                 double inv_zscale)
 {
@@ -396,6 +404,7 @@ __global__ void __launch_bounds__(kSmThreads) shadow_map_kernel(const rbsm_occlu
         oys[p] = __fsub_rn(small_int_float(ty + 8 * p), h);
     const long long n_all = (long long)occ.n_rects + occ.n_spheres;
     const long long pitch8 = pitch * 8;
+    unsigned round = 0;                        // culling rounds so far (selects the candidate buffer)
     // the tile's column and row, stepped by the grid stride (no division per
     // tile), and the offset of this thread's first row in the map
     const int tiles_x = (width + kTile - 1) / kTile;
@@ -424,13 +433,14 @@ __global__ void __launch_bounds__(kSmThreads) shadow_map_kernel(const rbsm_occlu
         for (int p = 0; p < 4; ++p)
             best[p] = occ.ground;
         // occluders in rounds of kChunk: rectangles, then spheres, in index
-        // order (the next round's first barrier keeps its survivors from
-        // overwriting these before every warp has read them)
+        // order
         for (long long base = 0; base < n_all; base += kChunk) {
             int nr, ns;
-            cull_round<COPIES>(occ, fop, fsp, base, tcx, tcy, fast, sm, nr, ns);
+            Cand *buf = sm.c[round & 1];
+            ++round;
+            cull_round<COPIES>(occ, fop, fsp, base, tcx, tcy, fast, sm, buf, nr, ns);
             for (int q = 0; q < nr; ++q) {
-                const RectCand &r = sm.c[q].r;
+                const RectCand &r = buf[sm.idx[q]].r;
                 const float sx = ox * r.uxf, tx_ = -ox * r.uyf;
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
@@ -441,29 +451,36 @@ __global__ void __launch_bounds__(kSmThreads) shadow_map_kernel(const rbsm_occlu
                         continue;                      // surely outside, or it cannot lower the depth
                     bool in = sf < r.haf - r.es && tf < r.hbf - r.et;
                     if (!in)
-                        in = rect_covers_exact(r, i, j0 + ty + 8 * p);     // near an edge
+                        in = rect_covers_exact(occ.rects + r.k, i, j0 + ty + 8 * p);     // near an edge
                     if (in)
                         best[p] = r.depth;
                 }
             }
             for (int q = 0; q < ns; ++q) {
-                const SphereCand &c = sm.c[nr + q].s;
+                const SphereCand &c = buf[sm.idx[nr + q]].s;
                 const float dxf = c.dx0 + ox;
                 const CapColumn col = cap_column(c, ox);
-#pragma unroll
+                // one copy of the cap code for the 4 rows (fewer registers):
+                // the rows' depths rotate through best[0]
+                float oy = oys[0];
+#pragma unroll 1
                 for (int p = 0; p < 4; ++p) {
-                    const float oy = oys[p];
                     const float dyf = c.dy0 + oy;
-                    if (!(c.dmin < best[p]) || dxf * dxf + dyf * dyf > c.r2f + c.e)
-                        continue;                      // cannot lower the depth, or surely outside the disc
-                    float d = 0.0f;
-                    const int cap = c.fast ? cap_fast(c, col, oy, invf, d) : -1;
-                    if (cap == 0)
-                        continue;
-                    if (cap < 0)
-                        d = cap_depth_exact(c, i, j0 + ty + 8 * p, inv_zscale, occ.zscale);
-                    if (d < best[p])
-                        best[p] = d;
+                    // skip when it cannot lower the depth, or surely outside the disc
+                    if (c.dmin < best[0] && !(dxf * dxf + dyf * dyf > c.r2f + c.e)) {
+                        float d = 0.0f;
+                        const int cap = c.fast ? cap_fast(c, col, oy, invf, d) : -1;
+                        if (cap < 0)
+                            d = cap_depth_exact(occ.spheres + c.k, i, j0 + ty + 8 * p, inv_zscale, occ.zscale);
+                        if (cap != 0 && d < best[0])
+                            best[0] = d;
+                    }
+                    const float b = best[0];
+                    best[0] = best[1];
+                    best[1] = best[2];
+                    best[2] = best[3];
+                    best[3] = b;
+                    oy = __fadd_rn(oy, 8.0f);              // exact
                 }
             }
         }
