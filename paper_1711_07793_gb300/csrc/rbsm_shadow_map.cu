@@ -87,7 +87,7 @@ struct TileSmem {
 // CTA, for the culling and the float pre-tests; `ea` bounds what the
 // rounding of the centre to float moves any projection (|c - c_f| (|ux| +
 // |uy|) <= (|cx| + |cy|) 2^-24 * sqrt 2, taken as 2^-22).
-constexpr int kFloatCopies = 384;
+constexpr int kFloatCopies = 256;
 struct FloatOcc {
     float cx, cy, ux, uy, ha, hb, ea, depth;
 };
@@ -371,7 +371,7 @@ __device__ __forceinline__ void cull_round(const rbsm_occluders &occ, const Floa
 // kFloatCopies); a compile-time choice, so that the culling holds no
 // double-to-float conversions (slow FP64 pipe) when it reads the copies.
 template <bool COPIES>
-__global__ void __launch_bounds__(kSmThreads, 3) shadow_map_kernel(const rbsm_occluders occ, float *__restrict__ depth,
+__global__ void __launch_bounds__(kSmThreads, 4) shadow_map_kernel(const rbsm_occluders occ, float *__restrict__ depth,
                                                                 int width, int height, long long pitch,
                                                                 double inv_zscale)
 {

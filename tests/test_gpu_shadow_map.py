@@ -120,7 +120,7 @@ def test_sphere_caps_against_the_oracle(api, zs):
     assert np.mean(ref < 2.0) > 0.15 and np.mean((ref > 0) & (ref < 2.0)) > 0.01
 
 
-@pytest.mark.parametrize("nr,ns", [(1100, 0), (0, 1100), (513, 1025), (384, 384), (385, 10)])
+@pytest.mark.parametrize("nr,ns", [(1100, 0), (0, 1100), (513, 1025), (256, 256), (257, 10), (384, 384)])
 def test_occluders_in_several_passes(api, nr, ns):
     """More than one pass of occluders of a kind (512 each): the running
     minimum is carried through the map between passes."""
