@@ -198,3 +198,21 @@ def test_generator_rasterises_exact_coverage():
     s = sc.Occluders(spheres=np.array([[16.0, 16.0, 5.0, 0.6]]))
     d = sc.raster(s, 32, 32, 32)
     assert d[15, 15] < 0.6 and d[0, 0] == 1.0
+
+
+def test_binding_rejects_bad_light_pass_outputs(native):
+    """The binding of rbsm_shadow_maps checks its outputs before the call:
+    one per occluder set, CUDA float32 (height, width) planes of one pitch."""
+    import torch
+    from paper_1711_07793_gb300 import api
+
+    class FakeOcc:
+        def desc(self, zscale, ground=1.0):
+            return native.rbsm_occluders(None, 0, None, 0, float(zscale), float(ground), 0)
+
+    with pytest.raises(ValueError):
+        api.rbsm_shadow_maps([FakeOcc(), FakeOcc()], 4, 4, 1.0, outs=[torch.zeros((4, 4))])
+    with pytest.raises(ValueError):
+        api.rbsm_shadow_maps([FakeOcc()], 4, 4, 1.0, outs=[torch.zeros((4, 4))])      # not a CUDA tensor
+    with pytest.raises(ValueError):
+        api.rbsm_shadow_maps([], 4, 4, 1.0, outs=[])
