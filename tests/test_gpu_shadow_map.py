@@ -178,3 +178,21 @@ def test_several_maps_in_one_call(api):
     api.rbsm_shadow_maps(occs, 1024, 1024, 1024.0, outs=[shared] * len(occs))
     torch.cuda.synchronize()
     assert same(shared.cpu().numpy(), singles[-1].cpu().numpy())
+
+
+@pytest.mark.parametrize("zs", [65536.0, 1000.0])
+def test_far_centres_at_the_maximum_extent(api, zs):
+    """Discs whose centres sit near x = 65536 (the largest map width), where
+    the float-float offsets carry the centre's magnitude: bit-exact against
+    the oracle at a power-of-two scale (float-float path) and another."""
+    w, h = 65536, 16
+    rng = np.random.default_rng(int(zs))
+    n = 40
+    sph = np.stack([rng.uniform(w - 3000, w + 5, n), rng.uniform(-4, h + 4, n), rng.uniform(0.6, 12, n),
+                    rng.uniform(0.3, 0.8, n)], 1)
+    sph[::4, 0:2] = np.floor(sph[::4, 0:2]) + 0.5
+    rects = np.array([[w - 100.25, 8.0, 0.6, 0.8, 40.0, 3.0]])
+    ref = orc.shadow_map(w, h, rects, [0.2], sph, zs, ground=1.0)
+    got = gpu_map(api, rects, [0.2], sph, w, h, zs, ground=1.0)
+    assert same(got, ref)
+    assert np.sum(ref < 1.0) > 1000
