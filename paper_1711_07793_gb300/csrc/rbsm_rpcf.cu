@@ -33,8 +33,8 @@ constexpr float kUnfix = 1.0f / 33554432.0f;   // 2^-25 (exact)
 constexpr uint32_t kNanFlag = 0x80000000u;     // above any sum (49 * 2^25 < 2^31): the mean is NaN
 // Edge samples are queued per fragment element: for k <= 3 all of a lane's
 // edge samples at once (a warp prefix sum places them), so the queue holds
-// < 32 left over + k^2 samples of every lane; for larger k one sample
-// position at a time (a ballot each), < 32 + 32.
+// < 32 left over + k^2 samples of every lane; for larger k each lane's
+// lowest remaining one per round (a ballot each), < 32 + 32.
 template <int K>
 struct RpcfQueue {
     static constexpr int kCap = K <= 3 ? 32 * K * K + 32 : 64;
@@ -241,14 +241,18 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
                     queued += (int)total;
                     drain(queued, false);
                 }
-            } else if (__any_sync(0xffffffffu, edges != 0)) {
-                // one sample position at a time
-#pragma unroll 1
-                for (int q = 0; q < K * K; ++q) {
-                    const bool eq = (edges >> q) & 1ull;
-                    const unsigned mask = __ballot_sync(0xffffffffu, eq);
-                    if (eq)
+            } else {
+                // each lane's lowest remaining edge sample per round: as many
+                // rounds as the most edge samples of any lane's fragment
+                uint64_t rest = edges;
+                while (__any_sync(0xffffffffu, rest != 0)) {
+                    const bool has = rest != 0;
+                    const unsigned mask = __ballot_sync(0xffffffffu, has);
+                    if (has) {
+                        const int q = __ffsll((long long)rest) - 1;
+                        rest &= rest - 1;
                         wq[warp].q[queued + __popc(mask & below)] = EdgeEntry{(uint32_t)(t.first + s), (uint32_t)q};
+                    }
                     queued += __popc(mask);
                     drain(queued, false);
                 }
