@@ -186,3 +186,35 @@ def test_bad_arguments(api):
         api.rbsm_visibility_gbuffer([api.GBufferJob(d, d, np.eye(4), mode=3)], mode=4)
     with pytest.raises(N.RBSMError):        # codes for some jobs only
         api.rbsm_visibility_gbuffer([api.GBufferJob(d, d, np.eye(4), codes=True), api.GBufferJob(d, d, np.eye(4))])
+
+
+def test_full_size_frames_in_one_call_as_the_bench_runs_them(api):
+    """Four full-size C5 frames (3840x2160 depth buffers, 8192^2 maps) as
+    jobs of one call, overlapped as dependent launches (the bench's launch
+    configuration): every answer equals that frame's single-job call bit for
+    bit, and a sample of one frame matches the oracle."""
+    import bench
+    c5, host = bench.make_workload(4, 0, pin=False)
+    maps = [dev(h["depth"].numpy()) for h in host]
+    bufs = []
+    for h in host:
+        d, m = c5.gbuffer(h["xyz"][2].numpy())
+        bufs.append((dev(d), m, d))
+    jobs = [api.GBufferJob(mp, g, m, mode=3, codes=True) for mp, (g, m, _) in zip(maps, bufs)]
+    api.rbsm_visibility_gbuffer(jobs)
+    singles = []
+    for mp, (g, m, _) in zip(maps, bufs):
+        j = api.GBufferJob(mp, g, m, mode=3, codes=True)
+        api.rbsm_visibility_gbuffer([j])
+        singles.append(j)
+    torch.cuda.synchronize()
+    for a, b in zip(jobs, singles):
+        assert torch.equal(a.vis_silhouette, b.vis_silhouette)
+        assert torch.equal(a.vis_filter, b.vis_filter)
+        assert torch.equal(a.codes, b.codes)
+    depth = host[2]["depth"].numpy()
+    x, y, zz = orc.project(bufs[2][2], bufs[2][1])
+    idx = np.sort(np.random.default_rng(2).choice(x.shape[0], 100000, replace=False))
+    ref_f = orc.evaluate(depth, x[idx], y[idx], zz[idx], 2)
+    assert np.array_equal(jobs[2].codes.cpu().numpy().view(np.uint16)[idx], ref_f["codes"])
+    assert np.abs(jobs[2].vis_filter.cpu().numpy()[idx].astype(np.float64) - ref_f["vis"]).max() <= TOL

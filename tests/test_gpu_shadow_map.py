@@ -196,3 +196,19 @@ def test_far_centres_at_the_maximum_extent(api, zs):
     got = gpu_map(api, rects, [0.2], sph, w, h, zs, ground=1.0)
     assert same(got, ref)
     assert np.sum(ref < 1.0) > 1000
+
+
+def test_full_size_maps_in_one_call_as_the_bench_runs_them(api):
+    """rbsm_shadow_maps over four full-size C5 maps (8192^2) in one call,
+    overlapped as dependent launches (the bench's launch configuration):
+    each map equals the generator's rasteriser bit for bit."""
+    import rbsm_scenes as sc
+    c5 = sc.Config5(0, frames=32)
+    frames = (3, 11, 19, 27)
+    occs = [c5.occluders(f) for f in frames]
+    dev_occs = [api.DeviceOccluders(o.rects, o.rect_depth, o.spheres) for o in occs]
+    outs = api.rbsm_shadow_maps(dev_occs, c5.size, c5.size, float(c5.size))
+    torch.cuda.synchronize()
+    for o, m in zip(occs, outs):
+        ref = sc.raster(o, c5.size, c5.size, c5.size)
+        assert same(m.cpu().numpy(), ref)
