@@ -440,6 +440,7 @@ def run_ours(args, rank, world, local_rank):
     learned = None
     if not args.skip_learned:
         learned = compare_learned(api, texs or maps, xyz, frames, n_frag, args, stream)
+        learned["training"] = measure_training(api, maps, xyz, args, stream)
 
     cpu = None
     edges = {}
@@ -549,6 +550,50 @@ def compare_learned(api, maps, xyz, frames, n_frag, args, stream):
             "error_vs_plain_answered": {"mean": float(dn.mean()) if dn.numel() else None, "p99": q(dn, 0.99),
                                         "max": float(dn.max()) if dn.numel() else None},
             "checkpoint": {k: net.header.get(k) for k in ("samples", "epochs", "data", "loss_per_epoch")}}
+
+
+def measure_training(api, maps, xyz, args, stream, batch=8192):
+    """The surrogate's training step on the tensor cores (rbsm_mlp_step: the
+    tcgen05 gradient kernel, then the fixed-order reduction fused with Adam)
+    over minibatches of edge fragments of the first two frames, and its
+    forward pass over every sample: time per step with CUDA events, samples
+    per second and the products' useful FLOP rate."""
+    import torch
+    from paper_1711_07793_gb300.surrogate import Surrogate
+    import rbsm_scenes as sc
+    data = [(maps[k], xyz[k][0], xyz[k][1], xyz[k][2]) for k in range(min(2, len(maps)))]
+    samples, count = Surrogate.dataset(data, capacity=1 << 20)
+    net = Surrogate(sc.mlp_init(0))
+    steps = max(20, min(args.steps, 400))
+    per_epoch = count // batch
+    perm = torch.randperm(count, generator=torch.Generator().manual_seed(3)).to(torch.int32).cuda()
+    orders = [perm[(s % per_epoch) * batch:(s % per_epoch + 1) * batch] for s in range(steps)]
+    for s in range(3):
+        net.train_step(samples, orders[s], 1e-3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s in range(steps):
+        net.train_step(samples, orders[s], 1e-3)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / steps
+    for _ in range(3):
+        net.forward(samples, count)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(20):
+        net.forward(samples, count)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_us = e0.elapsed_time(e1) * 1e3 / 20
+    # useful products per sample: forward 32x64 + 64x64 + 64x2, backward-data 2x64 + 64x64,
+    # weight gradients 32x64 + 64x64 + 64x2 multiply-adds
+    flops = 2 * (32 * 64 + 64 * 64 + 64 * 2) * 2 + 2 * (2 * 64 + 64 * 64)
+    return {"kernel": "rbsm::mlp::surrogate_tc_kernel (tcgen05, 128-sample tiles) + reduce_kernel (fixed order, Adam)",
+            "batch": batch, "samples": count, "steps_timed": steps, "us_per_step": us,
+            "samples_per_s": batch / (us * 1e-6), "useful_tflops": flops * batch / (us * 1e-6) / 1e12,
+            "forward": {"samples": count, "us": fwd_us, "gsamples_per_s": count / (fwd_us * 1e-6) / 1e9}}
 
 
 def measure_rpcf(api, maps, xyz, frames, n_frag, args, stream, k=3):

@@ -54,7 +54,9 @@ extern "C" {
 #define RBSM_OK 0
 #define RBSM_ERR_ARG (-1)          /* a NULL pointer, a size out of range, a bad mode */
 #define RBSM_ERR_CUDA (-2)         /* a CUDA call failed; see rbsm_last_cuda_error() */
-#define RBSM_ERR_TIMEOUT (-3)      /* a bounded device-side wait gave up */
+#define RBSM_ERR_TIMEOUT (-3)      /* a bounded device-side wait gave up (the tensor-core
+                                      surrogate kernels wait at most 1 s for their products;
+                                      rbsm_mlp_read reports it) */
 #define RBSM_ERR_WORKSPACE (-4)    /* workspace missing, too small or misaligned */
 
 #define RBSM_MODE_SILHOUETTE 1     /* Listing 4, §4.1: hard shadows, revectorised */
@@ -475,14 +477,19 @@ int rbsm_stager_destroy(rbsm_stager stager);
  * fragment from its 5x5 shadow-test pattern (bit (dy+2)*5 + (dx+2) set when
  * texel (i+dx, j+dy) is lit), its in-texel offsets and the depth gap to the
  * nearest blocker of the window, plus an estimate of its own absolute
- * error.  BF16 weights and activations, FP32 accumulation (tensor cores).
+ * error.  BF16 weights and activations, FP32 accumulation on the tensor
+ * cores: training and rbsm_mlp_forward on tcgen05 (tiles of 128 samples,
+ * accumulators in tensor memory), the guarded inference inside
+ * rbsm_batch_run on warp-level tiles of the edge fragments of one warp.
  *
  * The state block (device, caller-allocated, 256-byte aligned,
- * rbsm_mlp_state_bytes() bytes) holds the FP32 master parameters, their
- * gradient, the Adam moments, BF16 weight copies and a loss accumulator.
- * The FP32 parameter vector has RBSM_MLP_PARAMS floats in the order
- * W1 (32 x 64, row-major (in, out)), b1 (64), W2 (64 x 64), b2 (64),
- * W3 (64 x 2), b3 (2).
+ * rbsm_mlp_state_bytes() bytes, about 6.7 MB) holds the FP32 master
+ * parameters, their gradient, the Adam moments, BF16 weight copies, a loss
+ * accumulator, a status word and the per-CTA partial sums of the gradient
+ * kernel.  The FP32 parameter vector has RBSM_MLP_PARAMS floats in the
+ * order W1 (32 x 64, row-major (in, out)), b1 (64), W2 (64 x 64), b2 (64),
+ * W3 (64 x 2), b3 (2).  Calls on one state block must be ordered (one
+ * stream, or events); the gradient calls use the partials as scratch.
  */
 #define RBSM_MLP_PARAMS 6402
 
@@ -498,7 +505,7 @@ size_t rbsm_mlp_state_bytes(void);
 
 /* Copy n = RBSM_MLP_PARAMS host floats in (stream-ordered; the host array
  * must stay valid until the stream reaches the copy), zero the gradient,
- * the Adam moments and the loss, build the BF16 copies. */
+ * the Adam moments, the loss and the status word, build the BF16 copies. */
 int rbsm_mlp_load(void *state, const float *params_host, void *stream);
 
 /* Copy the FP32 master parameters out to host memory (stream-ordered). */
@@ -510,17 +517,29 @@ int rbsm_mlp_store(const void *state, float *params_host, void *stream);
 int rbsm_mlp_dataset(const rbsm_map *map, const rbsm_frags *frags, const rbsm_params *params,
                      rbsm_sample *samples, int64_t capacity, unsigned long long *counter, void *stream);
 
-/* Accumulate the loss gradient of one minibatch (samples[order[0..batch)])
- * into the state: loss = mean (y0 - t)^2 + mean (y1 - |clamp(y0,0,1) - t|)^2,
- * the second target held constant. */
+/* Add the loss gradient of one minibatch (samples[order[0..batch)], every
+ * order entry a valid sample index) to the state's gradient, and the loss
+ * sum to its loss accumulator: loss = mean (y0 - t)^2 + mean
+ * (y1 - |clamp(y0,0,1) - t|)^2, the second target held constant.  Two
+ * kernels: per-CTA sums over 128-sample tiles, then their sum in CTA order;
+ * the result is the same bits on every run. */
 int rbsm_mlp_grad(void *state, const rbsm_sample *samples, const int32_t *order, int32_t batch, void *stream);
+
+/* One training step: rbsm_mlp_grad of the minibatch followed by
+ * rbsm_mlp_adam(step, lr), with the reduction and the Adam update in one
+ * kernel (the same bits as the two calls). */
+int rbsm_mlp_step(void *state, const rbsm_sample *samples, const int32_t *order, int32_t batch, int32_t step,
+                  float lr, void *stream);
 
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr;
  * `step` counts from 1; clears the gradient. */
 int rbsm_mlp_adam(void *state, int32_t step, float lr, void *stream);
 
 /* Synchronously read the accumulated gradient (RBSM_MLP_PARAMS floats) and/or
- * the loss sum since the last reset (either pointer may be NULL). */
+ * the loss sum since the last reset (either pointer may be NULL).  Returns
+ * the RBSM_ERR_* code a surrogate kernel recorded in the state (a tensor-core
+ * wait that gave up: RBSM_ERR_TIMEOUT; the outputs are then not valid), else
+ * RBSM_OK. */
 int rbsm_mlp_read(const void *state, float *grad_host, float *loss_host, void *stream);
 int rbsm_mlp_reset_loss(void *state, void *stream);
 

@@ -169,6 +169,8 @@ def _declare(lib):
     lib.rbsm_mlp_dataset.argtypes = [_P(rbsm_map), _P(rbsm_frags), _P(rbsm_params), vp, ctypes.c_int64, vp, vp]
     lib.rbsm_mlp_grad.restype = i32
     lib.rbsm_mlp_grad.argtypes = [vp, vp, vp, ctypes.c_int32, vp]
+    lib.rbsm_mlp_step.restype = i32
+    lib.rbsm_mlp_step.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, vp]
     lib.rbsm_mlp_adam.restype = i32
     lib.rbsm_mlp_adam.argtypes = [vp, ctypes.c_int32, ctypes.c_float, vp]
     lib.rbsm_mlp_read.restype = i32

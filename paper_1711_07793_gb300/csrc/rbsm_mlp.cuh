@@ -2,10 +2,13 @@
 //
 // The surrogate is this project's addition (the paper has no network): a
 // 32-64-64-2 perceptron on the 5x5 shadow-test pattern of an edge fragment,
-// its in-texel offsets and its blocker-receiver depth gap.  Its matrix
-// products run on the tensor cores as warp-level mma.sync m16n8k16 tiles
-// with BF16 operands and FP32 accumulation; everything around them (bias,
-// ReLU, loss, guard) is FP32 on the CUDA cores.
+// its in-texel offsets and its blocker-receiver depth gap.  BF16 operands,
+// FP32 accumulation; everything around the products (bias, ReLU, loss,
+// guard) is FP32 on the CUDA cores.  Training and the stand-alone forward
+// pass run on tcgen05 (rbsm_learned.cu, 128-sample tiles); the guarded
+// inference inside the batched visibility kernel takes the edge fragments
+// of one warp, 32 at a time, with the warp-level mma.sync m16n8k16 tiles
+// below.
 //
 // Fragment layouts of mma.m16n8k16 (g = lane / 4, t = lane % 4):
 //   A (16 x 16, row-major): a0 = A[g][2t..2t+1], a1 = A[g+8][2t..2t+1],
@@ -43,9 +46,7 @@ constexpr int kParams = kOffB3 + kOut;           // 6402
 // BF16 copies the kernels read (elements).
 constexpr int kW1tElems = kHid * kIn;            // [out 64][in 32]   forward layer 1
 constexpr int kW2tElems = kHid * kHid;           // [out 64][in 64]   forward layer 2
-constexpr int kW2Elems = kHid * kHid;            // [in 64][out 64]   backward into h1
-constexpr int kW3tElems = kOutPad * kHid;        // [out 8][in 64]    forward layer 3
-constexpr int kW3Elems = kHid * 16;              // [in 64][out 16]   backward into h2
+constexpr int kW3tElems = kOutPad * kHid;        // [out 8][in 64]    forward layer 3 (rows 2..7 zero)
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
@@ -97,32 +98,6 @@ __device__ __forceinline__ void load_a(const uint16_t *a, int ld, int r0, int kt
     f[3] = *reinterpret_cast<const uint32_t *>(p + 8 * ld + 8);
 }
 
-// A fragment of the TRANSPOSE of a row-major BF16 matrix M[k][m] (pitch ld):
-// A[m][k] = M[k][m], m-tile [m0, m0+16), k-tile [k0, k0+16).
-__device__ __forceinline__ void load_a_trans(const uint16_t *mtx, int ld, int m0, int k0, unsigned lane,
-                                             uint32_t (&f)[4])
-{
-    const int g = lane >> 2, t = lane & 3;
-    auto at = [&](int m, int k) { return (uint32_t)mtx[k * ld + m]; };
-    const int m = m0 + g, k = k0 + 2 * t;
-    f[0] = at(m, k) | (at(m, k + 1) << 16);
-    f[1] = at(m + 8, k) | (at(m + 8, k + 1) << 16);
-    f[2] = at(m, k + 8) | (at(m, k + 9) << 16);
-    f[3] = at(m + 8, k + 8) | (at(m + 8, k + 9) << 16);
-}
-
-// B fragment (k-tile at k0, n-tile at n0) of a row-major BF16 matrix
-// M[k][n] (pitch ld): Bt[n][k] = M[k][n].
-__device__ __forceinline__ void load_b_rows(const uint16_t *mtx, int ld, int k0, int n0, unsigned lane,
-                                            uint32_t &b0, uint32_t &b1)
-{
-    const int g = lane >> 2, t = lane & 3;
-    auto at = [&](int k, int n) { return (uint32_t)mtx[k * ld + n]; };
-    const int n = n0 + g, k = k0 + 2 * t;
-    b0 = at(k, n) | (at(k + 1, n) << 16);
-    b1 = at(k + 8, n) | (at(k + 9, n) << 16);
-}
-
 // Layout of the network state block (bytes; sections 256-byte aligned).
 constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t kByteMaster = 0;
@@ -131,18 +106,26 @@ constexpr size_t kByteM = kByteGrad + align256(kParams * 4);
 constexpr size_t kByteV = kByteM + align256(kParams * 4);
 constexpr size_t kByteW1t = kByteV + align256(kParams * 4);
 constexpr size_t kByteW2t = kByteW1t + align256(kW1tElems * 2);
-constexpr size_t kByteW2 = kByteW2t + align256(kW2tElems * 2);
-constexpr size_t kByteW3t = kByteW2 + align256(kW2Elems * 2);
-constexpr size_t kByteW3 = kByteW3t + align256(kW3tElems * 2);
-constexpr size_t kByteLoss = kByteW3 + align256(kW3Elems * 2);
-constexpr size_t kStateBytes = kByteLoss + 256;
+constexpr size_t kByteW3t = kByteW2t + align256(kW2tElems * 2);
+constexpr size_t kByteLoss = kByteW3t + align256(kW3tElems * 2);
+// Training partials: one row per CTA of the gradient kernel, the CTA's sums
+// over its samples of every parameter's gradient (canonical order) and, at
+// index kParams, of the loss.  Reduced in a fixed order afterwards, so a
+// gradient does not depend on which CTA finishes first.
+constexpr int kPartStride = 6464;                // floats per CTA row (>= kParams + 1)
+constexpr int kMaxGradCtas = 256;
+constexpr size_t kBytePart = kByteLoss + 256;
+constexpr size_t kStateBytes = kBytePart + (size_t)kMaxGradCtas * kPartStride * 4;
 constexpr size_t kByteBf16 = kByteW1t;
 constexpr size_t kBf16Bytes = kByteLoss - kByteW1t;
+static_assert(kPartStride >= kParams + 1, "partial row holds every parameter and the loss");
 
 struct State {
     float *master, *grad, *m, *v;
-    uint16_t *w1t, *w2t, *w2, *w3t, *w3;
+    uint16_t *w1t, *w2t, *w3t;
     float *loss;              // [0] sum of per-sample losses, [1] samples
+    unsigned *status;         // RBSM_ERR_* recorded by a kernel (0 = none)
+    float *part;              // kMaxGradCtas x kPartStride training partials
 };
 
 __host__ __device__ inline State state_of(void *base)
@@ -151,8 +134,8 @@ __host__ __device__ inline State state_of(void *base)
     return State{reinterpret_cast<float *>(b + kByteMaster), reinterpret_cast<float *>(b + kByteGrad),
                  reinterpret_cast<float *>(b + kByteM), reinterpret_cast<float *>(b + kByteV),
                  reinterpret_cast<uint16_t *>(b + kByteW1t), reinterpret_cast<uint16_t *>(b + kByteW2t),
-                 reinterpret_cast<uint16_t *>(b + kByteW2), reinterpret_cast<uint16_t *>(b + kByteW3t),
-                 reinterpret_cast<uint16_t *>(b + kByteW3), reinterpret_cast<float *>(b + kByteLoss)};
+                 reinterpret_cast<uint16_t *>(b + kByteW3t), reinterpret_cast<float *>(b + kByteLoss),
+                 reinterpret_cast<unsigned *>(b + kByteLoss + 16), reinterpret_cast<float *>(b + kBytePart)};
 }
 
 // Weights of one network as the kernels read them (shared memory).

@@ -114,6 +114,13 @@ class Surrogate:
         self.step += 1
         N.check("rbsm_mlp_adam", N.lib().rbsm_mlp_adam(_ptr(self.state), self.step, float(lr), _stream_handle(None)))
 
+    def train_step(self, samples, order, lr):
+        """Gradient of one minibatch and the Adam step, in two kernels."""
+        self.step += 1
+        N.check("rbsm_mlp_step", N.lib().rbsm_mlp_step(_ptr(self.state), _ptr(samples), _ptr(order),
+                                                       int(order.numel()), self.step, float(lr),
+                                                       _stream_handle(None)))
+
     def read_grad(self):
         g = torch.empty(N_PARAMS, dtype=torch.float32, pin_memory=True)
         N.check("rbsm_mlp_read", N.lib().rbsm_mlp_read(_ptr(self.state), _ptr(g), None, _stream_handle(None)))
@@ -136,8 +143,7 @@ class Surrogate:
             perm = torch.from_numpy(rng.permutation(count).astype(np.int32)).to(self.device)
             self.take_loss()
             for s in range(steps_per_epoch):
-                self.grad(samples, perm[s * batch:(s + 1) * batch])
-                self.adam(lr)
+                self.train_step(samples, perm[s * batch:(s + 1) * batch], lr)
             history.append(self.take_loss() / (steps_per_epoch * batch))
             if log:
                 log("epoch %d loss %.6f lr %.2e" % (ep, history[-1], lr))
