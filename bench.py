@@ -59,7 +59,7 @@ def parse_args(argv=None):
     p.add_argument("--skip-sweep", action="store_true", help="profiling runs only")
     p.add_argument("--configs", action="store_true",
                    help="one line per workload C1-C4 (GPU rate, roofline, oracle on 1 and all threads)")
-    p.add_argument("--guard-tau", type=float, default=0.05, help="surrogate guard (largest accepted error estimate)")
+    p.add_argument("--guard-tau", type=float, default=0.01, help="surrogate guard (largest accepted error estimate)")
     p.add_argument("--texture", choices=["on", "off"], default="on",
                    help="read each map's four-neighbourhood with texture gathers (rbsm_map_texture_create)")
     p.add_argument("--graph", choices=["on", "off"], default="on",
@@ -491,6 +491,9 @@ def run_ours(args, rank, world, local_rank):
 # ---------------------------------------------------------------- learned --
 
 CHECKPOINT = os.path.join(ROOT, "paper_1711_07793_gb300", "weights", "surrogate_c4.npz")
+# the surrogate's stated bound on the answers it gives (|error| against the
+# exact Listing 5 answer) at guard_tau = 0.01
+SURROGATE_BOUND = {"mean": 0.01, "p99": 0.03, "max": 0.1}
 
 
 def compare_learned(api, maps, xyz, frames, n_frag, args, stream):
@@ -540,6 +543,9 @@ def compare_learned(api, maps, xyz, frames, n_frag, args, stream):
         k = max(1, int(round(p * t.numel())))
         return float(torch.kthvalue(t.cpu(), k).values)
     fps = lambda ms: frames * n_frag / (ms * 1e-3) / 1e9
+    answered = {"mean": float(dn.mean()) if dn.numel() else None, "p99": q(dn, 0.99),
+                "max": float(dn.max()) if dn.numel() else None}
+    met = all(answered[k] is not None and answered[k] <= v for k, v in SURROGATE_BOUND.items())
     return {"metric": "Gfragments/s RSMSS (filtering) visibility, same frames, one batched launch per step",
             "plain": {"value": fps(ms_plain), "ms_per_step": ms_plain},
             "learned": {"value": fps(ms_learned), "ms_per_step": ms_learned, "guard_tau": args.guard_tau},
@@ -547,8 +553,11 @@ def compare_learned(api, maps, xyz, frames, n_frag, args, stream):
             "edge_fragments": acc + fb, "surrogate_answers": acc, "fallbacks": fb,
             "fallback_frac": fb / max(1, acc + fb),
             "error_vs_plain_all": {"mean": float(d.mean()), "p99": q(d, 0.99), "max": float(d.max())},
-            "error_vs_plain_answered": {"mean": float(dn.mean()) if dn.numel() else None, "p99": q(dn, 0.99),
-                                        "max": float(dn.max()) if dn.numel() else None},
+            "error_vs_plain_answered": answered,
+            "stated_bound": dict(SURROGATE_BOUND, guard_tau=0.01,
+                                 guards="walks inside the 5x5 window, trusted pattern (calibrated bitmap), "
+                                        "error estimate <= guard_tau"),
+            "bound_met": met if args.guard_tau <= 0.01 else None,
             "checkpoint": {k: net.header.get(k) for k in ("samples", "epochs", "data", "loss_per_epoch")}}
 
 

@@ -105,8 +105,12 @@ typedef struct {
 
 typedef struct {
     int32_t max_dist;              /* MAXDIST of Listing 3, 1..RBSM_MAXDIST_LIMIT */
-    int32_t flags;                 /* reserved, must be 0 */
+    int32_t flags;                 /* 0; rbsm_mlp_dataset also takes RBSM_DATASET_IN_WINDOW */
 } rbsm_params;
+
+/* rbsm_mlp_dataset: keep only edge fragments whose Listing 3 walks stop
+ * inside the 5x5 window (the fragments the batch's surrogate may answer). */
+#define RBSM_DATASET_IN_WINDOW 1
 
 /*
  * Silhouette recovery (Listing 1 with Listings 2-4; §3.1 and §4.1).
@@ -236,9 +240,13 @@ typedef struct {
                                     * the third */
     /* Learned penumbra (not in the paper): NULL = exact everywhere.  Given a
      * network state block (rbsm_mlp_state_bytes), FILTER-mode jobs answer
-     * their edge fragments with the surrogate wherever its own error
-     * estimate is <= guard_tau (0 <= guard_tau < 1e30) and fall back to
-     * the exact walk elsewhere;
+     * an edge fragment with the surrogate when (1) its four Listing 3 walks
+     * stop inside the 5x5 window the network sees (read from the window's
+     * shadow-test pattern; otherwise the exact answer depends on texels the
+     * network cannot see), (2) its pattern is trusted (rbsm_mlp_set_trust;
+     * all are when no bitmap is in force) and (3) the network's own error
+     * estimate is <= guard_tau (0 <= guard_tau < 1e30); every other edge
+     * fragment falls back to the exact walk;
      * shadow tests, discontinuity codes and off-edge answers stay exact, and
      * SILHOUETTE / BOTH jobs are not touched.  A surrogate answer's code has
      * bit 10 set and no end counts (bits 5-9 clear). */
@@ -483,12 +491,12 @@ int rbsm_stager_destroy(rbsm_stager stager);
  * rbsm_batch_run on warp-level tiles of the edge fragments of one warp.
  *
  * The state block (device, caller-allocated, 256-byte aligned,
- * rbsm_mlp_state_bytes() bytes, about 6.7 MB) holds the FP32 master
+ * rbsm_mlp_state_bytes() bytes, about 11 MB) holds the FP32 master
  * parameters, their gradient, the Adam moments, BF16 weight copies, a loss
- * accumulator, a status word and the per-CTA partial sums of the gradient
- * kernel.  The FP32 parameter vector has RBSM_MLP_PARAMS floats in the
- * order W1 (32 x 64, row-major (in, out)), b1 (64), W2 (64 x 64), b2 (64),
- * W3 (64 x 2), b3 (2).  Calls on one state block must be ordered (one
+ * accumulator, a status word, the per-CTA partial sums of the gradient
+ * kernel and the trusted-pattern bitmap.  The FP32 parameter vector has
+ * RBSM_MLP_PARAMS floats in the order W1 (32 x 64, row-major (in, out)),
+ * b1 (64), W2 (64 x 64), b2 (64), W3 (64 x 2), b3 (2).  Calls on one state block must be ordered (one
  * stream, or events); the gradient calls use the partials as scratch.
  */
 #define RBSM_MLP_PARAMS 6402
@@ -508,12 +516,25 @@ size_t rbsm_mlp_state_bytes(void);
  * the Adam moments, the loss and the status word, build the BF16 copies. */
 int rbsm_mlp_load(void *state, const float *params_host, void *stream);
 
+/* Trusted patterns: a bitmap of RBSM_MLP_TRUST_WORDS host words (bit p & 31
+ * of word p >> 5 for the 25-bit 5x5 pattern p), copied in stream-ordered;
+ * from then on rbsm_batch_run lets the surrogate answer only fragments whose
+ * pattern is trusted.  NULL switches the bitmap off (every pattern trusted,
+ * the state after rbsm_mlp_load).  The bitmap comes from calibration: the
+ * patterns on which the trained network's answers stayed within a stated
+ * error over held-out calibration scenes. */
+#define RBSM_MLP_TRUST_WORDS (1 << 20)
+int rbsm_mlp_set_trust(void *state, const uint32_t *bitmap_host, void *stream);
+
 /* Copy the FP32 master parameters out to host memory (stream-ordered). */
 int rbsm_mlp_store(const void *state, float *params_host, void *stream);
 
 /* Append every edge fragment of a fragment set (filtering mode) as a
  * training sample at the device counter *counter (which the caller zeroes
- * once); samples past `capacity` are counted but not written. */
+ * once); samples past `capacity` are counted but not written.  With
+ * params->flags = RBSM_DATASET_IN_WINDOW only the fragments whose walks stop
+ * inside the 5x5 window are kept.  The order of the samples is not fixed
+ * (warps append as they finish). */
 int rbsm_mlp_dataset(const rbsm_map *map, const rbsm_frags *frags, const rbsm_params *params,
                      rbsm_sample *samples, int64_t capacity, unsigned long long *counter, void *stream);
 

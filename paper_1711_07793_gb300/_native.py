@@ -16,6 +16,8 @@ RBSM_OK = 0
 RBSM_ERR_ARG = -1
 RBSM_ERR_CUDA = -2
 RBSM_ERR_TIMEOUT = -3
+RBSM_DATASET_IN_WINDOW = 1
+RBSM_MLP_TRUST_WORDS = 1 << 20
 RBSM_ERR_WORKSPACE = -4
 
 RBSM_MODE_SILHOUETTE = 1
@@ -169,6 +171,8 @@ def _declare(lib):
     lib.rbsm_mlp_dataset.argtypes = [_P(rbsm_map), _P(rbsm_frags), _P(rbsm_params), vp, ctypes.c_int64, vp, vp]
     lib.rbsm_mlp_grad.restype = i32
     lib.rbsm_mlp_grad.argtypes = [vp, vp, vp, ctypes.c_int32, vp]
+    lib.rbsm_mlp_set_trust.restype = i32
+    lib.rbsm_mlp_set_trust.argtypes = [vp, vp, vp]
     lib.rbsm_mlp_step.restype = i32
     lib.rbsm_mlp_step.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, vp]
     lib.rbsm_mlp_adam.restype = i32

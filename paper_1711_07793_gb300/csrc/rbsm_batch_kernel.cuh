@@ -88,14 +88,16 @@ struct LearnedSmem {
     uint16_t feat[kThreads / 32][32 * mlp::kIn];
     float out[kThreads / 32][32 * mlp::kOut];
     EdgeEntry fallback[kThreads / 32][64];      // guard-tripped fragments: < 32 left over + one round
+    const uint32_t *trust;                      // trusted-pattern bitmap, or nullptr (none in force)
 };
 
 // Drain rounds of up to 32 queued edge fragments with the surrogate: each
 // lane gathers its fragment's 5x5 features into one input row, the warp runs
 // the network on the 32 rows (two m16 tiles on the tensor cores), and each
-// fragment whose error estimate is within the guard takes the estimate,
-// clamped to [0, 1]; the others (and every fragment of a job that is not in
-// FILTER mode) go to the warp's fallback queue, whose exact walks run in
+// fragment whose walks stop inside the window, whose pattern is trusted and
+// whose error estimate is within the guard takes the estimate, clamped to
+// [0, 1]; the others (and every fragment of a job that is not in FILTER
+// mode) go to the warp's fallback queue, whose exact walks run in
 // rounds of 32 like the exact path's (walked in place, a round's few
 // fallbacks would keep most lanes idle through the walk).
 template <typename Jobs, int kThreads>
@@ -134,10 +136,12 @@ __device__ __forceinline__ void drain_queue_learned(const Jobs &jobs, WarpQueue 
             o = jobs((int)(q.bits_job >> 8));
         }
         const bool use_net = valid && o.mode == 2;
+        bool in_window = false;
         if (use_net) {
             uint32_t bits;
             float fx, fy, gap;
             fragment_features(o.map, __ldg(o.x + q.idx), __ldg(o.y + q.idx), __ldg(o.z + q.idx), bits, fx, fy, gap);
+            in_window = walks_inside_window(bits, max_dist) && mlp::pattern_trusted(ls.trust, bits);
             mlp::write_input_row(feat + lane * mlp::kIn, bits, fx, fy, gap);
         } else {
             uint4 *row = reinterpret_cast<uint4 *>(feat + lane * mlp::kIn);
@@ -168,7 +172,11 @@ __device__ __forceinline__ void drain_queue_learned(const Jobs &jobs, WarpQueue 
         bool accepted = false;
         if (use_net) {
             const float v = yout[lane * 2], e = yout[lane * 2 + 1];
-            accepted = e <= tau && v == v;          // a NaN estimate never passes
+            // structural guard: the answer must be a function of what the
+            // network sees, and its pattern trusted by calibration (when a
+            // bitmap is in force); then the network's own error estimate (a
+            // NaN never passes)
+            accepted = in_window && e <= tau && v == v;
             if (accepted) {
                 const float vc = v < 0.0f ? 0.0f : (v > 1.0f ? 1.0f : v);
                 o.fil[q.idx] = vc;
@@ -245,6 +253,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const __gri
         }
         for (int k = threadIdx.x; k < mlp::kOutPad; k += kThreads)
             ls.w.b3[k] = k < mlp::kOut ? st.master[mlp::kOffB3 + k] : 0.0f;
+        if (threadIdx.x == 0)
+            ls.trust = *st.trust_on ? st.trust : nullptr;
         __syncthreads();
     }
     WarpQueue &wq = bs.queue[warp];

@@ -224,6 +224,31 @@ __device__ __forceinline__ void fragment_features(const MapDev &m, float x, floa
     gap = __fsub_rn(pz, zmin);
 }
 
+// Whether the four Listing 3 walks from the fragment's texel stop inside its
+// 5x5 window, read from the window's shadow-test pattern (bit (dy+2)*5 +
+// (dx+2): texel (i+dx, j+dy) lit).  A walk along x goes on past step k when
+// texel (k, 0) has the fragment's test and shares a discontinuity
+// direction with the fragment's texel; along a continuing walk only the
+// perpendicular directions can be shared (the +-y neighbours of (k, 0)
+// against those of (0, 0)).  Steps 1 and 2 read only window texels, so when
+// no walk goes on past step 2 (or max_dist <= 2) the exact answer is a
+// function of the pattern and the in-texel offsets alone; otherwise it
+// depends on texels the window does not hold.
+__device__ __forceinline__ bool walks_inside_window(uint32_t pattern, int max_dist)
+{
+    if (max_dist <= 2)
+        return true;
+    const uint32_t s0 = (pattern >> 12) & 1u;
+    // d[k] = bit k of "texel differs from the fragment's test"
+    const uint32_t d = pattern ^ (s0 ? 0x1FFFFFFu : 0u);
+    auto diff = [&](int dx, int dy) { return (d >> ((dy + 2) * 5 + (dx + 2))) & 1u; };
+    const uint32_t up0 = diff(0, 1), dn0 = diff(0, -1), lf0 = diff(-1, 0), rt0 = diff(1, 0);
+    auto goes_on_x = [&](int dx) { return !diff(dx, 0) && ((up0 & diff(dx, 1)) | (dn0 & diff(dx, -1))); };
+    auto goes_on_y = [&](int dy) { return !diff(0, dy) && ((lf0 & diff(-1, dy)) | (rt0 & diff(1, dy))); };
+    return !(goes_on_x(1) && goes_on_x(2)) && !(goes_on_x(-1) && goes_on_x(-2)) &&
+           !(goes_on_y(1) && goes_on_y(2)) && !(goes_on_y(-1) && goes_on_y(-2));
+}
+
 // Result of one fragment.
 struct FragResult {
     float sil;

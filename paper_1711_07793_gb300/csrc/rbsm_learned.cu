@@ -52,8 +52,10 @@ __global__ void refresh_kernel(void *base)
     }
     if (blockIdx.x == 0 && threadIdx.x < 2)
         s.loss[threadIdx.x] = 0.0f;
-    if (blockIdx.x == 0 && threadIdx.x == 0)
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         *s.status = 0u;
+        *s.trust_on = 0u;
+    }
 }
 
 // One Adam update (Kingma and Ba, Algorithm 1) of parameter p with gradient
@@ -88,8 +90,8 @@ __global__ void adam_kernel(void *base, float lr, float bc1, float bc2)
 // with its features and its exact RSMSS answer, appended at an atomic
 // counter (warp-aggregated).  Samples past `capacity` are counted, not kept.
 __global__ void dataset_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict__ y,
-                               const float *__restrict__ z, long long n, int max_dist, rbsm_sample *out,
-                               long long capacity, unsigned long long *counter)
+                               const float *__restrict__ z, long long n, int max_dist, bool in_window_only,
+                               rbsm_sample *out, long long capacity, unsigned long long *counter)
 {
     const unsigned lane = lane_id();
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -99,11 +101,17 @@ __global__ void dataset_kernel(const MapDev m, const float *__restrict__ x, cons
         FragResult r{0.0f, 0.0f, 0};
         uint32_t bits = 0;
         float xv = 0.0f, yv = 0.0f, zv = 0.0f;
+        rbsm_sample smp;
         if (k < n) {
             xv = x[k];
             yv = y[k];
             zv = z[k];
             edge = classify<2, false>(m, xv, yv, zv, r, bits);
+            if (edge) {
+                fragment_features(m, xv, yv, zv, smp.bits, smp.fx, smp.fy, smp.gap);
+                if (in_window_only && !walks_inside_window(smp.bits, max_dist))
+                    edge = false;
+            }
         }
         const unsigned mask = __ballot_sync(0xffffffffu, edge);
         if (mask == 0)
@@ -119,8 +127,6 @@ __global__ void dataset_kernel(const MapDev m, const float *__restrict__ x, cons
         if ((long long)slot >= capacity)
             continue;
         resolve_edge<2>(m, xv, yv, zv, bits, max_dist, r);
-        rbsm_sample smp;
-        fragment_features(m, xv, yv, zv, smp.bits, smp.fx, smp.fy, smp.gap);
         smp.label = r.fil;
         out[slot] = smp;
     }
@@ -317,6 +323,17 @@ surrogate_tc_kernel(void *base, const rbsm_sample *__restrict__ data, const int 
     asm volatile("griddepcontrol.wait;" ::: "memory");
 
     const State st = state_of(base);
+    const long long tiles = (n + kTcRows - 1) / kTcRows;
+    // a tile's samples are gathered one tile ahead (the first before the
+    // weights are staged), so the gather overlaps the previous tile's products
+    auto gather = [&](long long tile) {
+        rbsm_sample v{0u, 0.0f, 0.0f, 0.0f, 0.0f};
+        const long long b = tile * kTcRows + tid;
+        if (tile < tiles && b < n)
+            v = data[kTrain ? (long long)order[b] : b];
+        return v;
+    };
+    rbsm_sample smp = gather(blockIdx.x);
     stage_weights(sm.w1t, st.w1t, kHid, kHid, kIn);
     stage_weights(sm.w2t, st.w2t, kHid, kHid, kHid);
     stage_weights(sm.w3t, st.w3t, kW3Rows, kOutPad, kHid);
@@ -344,13 +361,9 @@ surrogate_tc_kernel(void *base, const rbsm_sample *__restrict__ data, const int 
     uint32_t parity = 0;
     bool first = true, p1_pending = false;
     float db1 = 0.0f, db2 = 0.0f, db3 = 0.0f, loss = 0.0f;    // thread t: column t of b1 / b2 (t < 64), b3 (t < 2)
-    const long long tiles = (n + kTcRows - 1) / kTcRows;
     for (long long tile = blockIdx.x; tile < tiles && !fail; tile += gridDim.x) {
         const long long b = tile * kTcRows + tid;
         const bool valid = b < n;
-        rbsm_sample smp{0u, 0.0f, 0.0f, 0.0f, 0.0f};
-        if (valid)
-            smp = data[kTrain ? (long long)order[b] : b];
         if (p1_pending) {       // the previous tile's weight-gradient products still read act and grd
             const bool ok = wait_products(&sm.bar, parity);
             p1_pending = false;
@@ -374,6 +387,8 @@ surrogate_tc_kernel(void *base, const rbsm_sample *__restrict__ data, const int 
                 *reinterpret_cast<uint4 *>(group_ptr(sm.act, kActSbo, tid, kGX + g)) =
                     make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
         }
+        const float label = smp.label;
+        smp = gather(tile + gridDim.x);
         if ((fail = sync_for_mma(false)))
             break;
         // ---- layer 1: a1 = X W1 (K = 32)
@@ -431,7 +446,7 @@ surrogate_tc_kernel(void *base, const rbsm_sample *__restrict__ data, const int 
                 // loss and output gradient: (y0 - t)^2 + (y1 - |clamp(y0) - t|)^2, the second target constant
                 float dy0 = 0.0f, dy1 = 0.0f, l = 0.0f;
                 if (valid) {
-                    const float tl = smp.label;
+                    const float tl = label;
                     const float vc = fminf(fmaxf(y0, 0.0f), 1.0f);
                     const float et = fabsf(vc - tl);
                     const float rv = y0 - tl, re = y1 - et;
@@ -677,6 +692,20 @@ int rbsm_mlp_load(void *state, const float *params, void *stream)
     return e == cudaSuccess ? RBSM_OK : cuda_fail(e);
 }
 
+int rbsm_mlp_set_trust(void *state, const uint32_t *bitmap, void *stream)
+{
+    if (!state || (reinterpret_cast<uintptr_t>(state) & 255u))
+        return RBSM_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const mlp::State st = mlp::state_of(state);
+    cudaError_t e = cudaSuccess;
+    if (bitmap)
+        e = cudaMemcpyAsync(st.trust, bitmap, (size_t)mlp::kTrustWords * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(st.trust_on, bitmap ? 1 : 0, sizeof(unsigned), s);
+    return e == cudaSuccess ? RBSM_OK : cuda_fail(e);
+}
+
 int rbsm_mlp_store(const void *state, float *params, void *stream)
 {
     if (!state || !params)
@@ -693,9 +722,13 @@ int rbsm_mlp_dataset(const rbsm_map *map, const rbsm_frags *frags, const rbsm_pa
     int rc, max_dist;
     if ((rc = check_map(map)) != RBSM_OK) return rc;
     if ((rc = check_frags(frags)) != RBSM_OK) return rc;
-    if ((rc = check_params(params, &max_dist)) != RBSM_OK) return rc;
+    if (!params || (params->flags & ~RBSM_DATASET_IN_WINDOW))
+        return RBSM_ERR_ARG;
+    const rbsm_params plain{params->max_dist, 0};
+    if ((rc = check_params(&plain, &max_dist)) != RBSM_OK) return rc;
     if (!counter || capacity < 0 || (capacity > 0 && !samples))
         return RBSM_ERR_ARG;
+    const bool in_window_only = (params->flags & RBSM_DATASET_IN_WINDOW) != 0;
     if (frags->n == 0)
         return RBSM_OK;
     const int sms = device_sm_count();
@@ -705,7 +738,7 @@ int rbsm_mlp_dataset(const rbsm_map *map, const rbsm_frags *frags, const rbsm_pa
     if (blocks > (long long)sms * 8)
         blocks = (long long)sms * 8;
     mlp::dataset_kernel<<<(unsigned)blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-        to_dev(*map), frags->x, frags->y, frags->z, frags->n, max_dist, samples, capacity, counter);
+        to_dev(*map), frags->x, frags->y, frags->z, frags->n, max_dist, in_window_only, samples, capacity, counter);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? RBSM_OK : cuda_fail(e);
 }

@@ -115,7 +115,12 @@ constexpr size_t kByteLoss = kByteW3t + align256(kW3tElems * 2);
 constexpr int kPartStride = 6464;                // floats per CTA row (>= kParams + 1)
 constexpr int kMaxGradCtas = 256;
 constexpr size_t kBytePart = kByteLoss + 256;
-constexpr size_t kStateBytes = kBytePart + (size_t)kMaxGradCtas * kPartStride * 4;
+// Trusted 5x5 shadow-test patterns: one bit per 25-bit pattern (bit p & 31
+// of word p >> 5), set by calibration; consulted when the trust word of the
+// loss section is nonzero.
+constexpr int kTrustWords = 1 << 20;
+constexpr size_t kByteTrust = kBytePart + align256((size_t)kMaxGradCtas * kPartStride * 4);
+constexpr size_t kStateBytes = kByteTrust + (size_t)kTrustWords * 4;
 constexpr size_t kByteBf16 = kByteW1t;
 constexpr size_t kBf16Bytes = kByteLoss - kByteW1t;
 static_assert(kPartStride >= kParams + 1, "partial row holds every parameter and the loss");
@@ -126,6 +131,8 @@ struct State {
     float *loss;              // [0] sum of per-sample losses, [1] samples
     unsigned *status;         // RBSM_ERR_* recorded by a kernel (0 = none)
     float *part;              // kMaxGradCtas x kPartStride training partials
+    unsigned *trust_on;       // nonzero: the trust bitmap is in force
+    uint32_t *trust;          // kTrustWords words
 };
 
 __host__ __device__ inline State state_of(void *base)
@@ -135,7 +142,14 @@ __host__ __device__ inline State state_of(void *base)
                  reinterpret_cast<float *>(b + kByteM), reinterpret_cast<float *>(b + kByteV),
                  reinterpret_cast<uint16_t *>(b + kByteW1t), reinterpret_cast<uint16_t *>(b + kByteW2t),
                  reinterpret_cast<uint16_t *>(b + kByteW3t), reinterpret_cast<float *>(b + kByteLoss),
-                 reinterpret_cast<unsigned *>(b + kByteLoss + 16), reinterpret_cast<float *>(b + kBytePart)};
+                 reinterpret_cast<unsigned *>(b + kByteLoss + 16), reinterpret_cast<float *>(b + kBytePart),
+                 reinterpret_cast<unsigned *>(b + kByteLoss + 20), reinterpret_cast<uint32_t *>(b + kByteTrust)};
+}
+
+// Whether a 5x5 pattern is trusted (always, when no bitmap is in force).
+__device__ __forceinline__ bool pattern_trusted(const uint32_t *trust, uint32_t pattern)
+{
+    return trust == nullptr || ((__ldg(trust + (pattern >> 5)) >> (pattern & 31u)) & 1u) != 0;
 }
 
 // Weights of one network as the kernels read them (shared memory).

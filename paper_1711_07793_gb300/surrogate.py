@@ -61,9 +61,34 @@ class Surrogate:
         if vec.shape != (N_PARAMS,):
             raise ValueError("expected %d parameters" % N_PARAMS)
         self.step = 0
+        self.trust = None
         self._host = torch.from_numpy(vec.copy()).pin_memory()
         N.check("rbsm_mlp_load", N.lib().rbsm_mlp_load(_ptr(self.state), _ptr(self._host), _stream_handle(None)))
         torch.cuda.current_stream().synchronize()
+
+    def set_trust(self, bitmap):
+        """Trusted-pattern bitmap (uint32 array of RBSM_MLP_TRUST_WORDS words;
+        bit p & 31 of word p >> 5 for pattern p), or None for none."""
+        if bitmap is None:
+            self.trust = None
+            N.check("rbsm_mlp_set_trust", N.lib().rbsm_mlp_set_trust(_ptr(self.state), None, _stream_handle(None)))
+        else:
+            bitmap = np.ascontiguousarray(bitmap, np.uint32)
+            if bitmap.shape != (N.RBSM_MLP_TRUST_WORDS,):
+                raise ValueError("expected %d words" % N.RBSM_MLP_TRUST_WORDS)
+            self.trust = bitmap
+            host = torch.from_numpy(bitmap.view(np.int32)).pin_memory()
+            N.check("rbsm_mlp_set_trust", N.lib().rbsm_mlp_set_trust(_ptr(self.state), _ptr(host),
+                                                                     _stream_handle(None)))
+        torch.cuda.current_stream().synchronize()
+
+    @staticmethod
+    def trust_bitmap(patterns):
+        """Bitmap with the bits of the given 25-bit patterns set."""
+        p = np.unique(np.asarray(patterns, np.uint32))
+        words = np.zeros(N.RBSM_MLP_TRUST_WORDS, np.uint32)
+        np.bitwise_or.at(words, p >> 5, np.left_shift(np.uint32(1), p & np.uint32(31)))
+        return words
 
     def params(self):
         out = torch.empty(N_PARAMS, dtype=torch.float32, pin_memory=True)
@@ -73,14 +98,16 @@ class Surrogate:
 
     # --------------------------------------------------------------- data --
     @staticmethod
-    def dataset(maps_frags, capacity, max_dist=N.RBSM_MAXDIST_DEFAULT, device="cuda"):
+    def dataset(maps_frags, capacity, max_dist=N.RBSM_MAXDIST_DEFAULT, device="cuda", in_window=False):
         """Training samples (a uint8 tensor of capacity x 20 bytes) from every
-        edge fragment of the given (depth, x, y, z) CUDA tensors, in order,
-        until `capacity`; returns (samples, count)."""
+        edge fragment of the given (depth, x, y, z) CUDA tensors (with
+        in_window, only those whose walks stop inside the 5x5 window), until
+        `capacity`; returns (samples, count)."""
         samples = torch.empty(capacity * SAMPLE_BYTES, dtype=torch.uint8, device=device)
         counter = torch.zeros(1, dtype=torch.int64, device=device)
         for depth, x, y, z in maps_frags:
             m, f, p = map_desc(depth), frags_desc(x, y, z), _params(max_dist)
+            p.flags = N.RBSM_DATASET_IN_WINDOW if in_window else 0
             N.check("rbsm_mlp_dataset",
                     N.lib().rbsm_mlp_dataset(ctypes.byref(m), ctypes.byref(f), ctypes.byref(p), _ptr(samples),
                                              capacity, _ptr(counter), _stream_handle(None)))
@@ -161,7 +188,8 @@ class Surrogate:
         """Parameters (float32) plus a header: dims, Adam step, caller's meta."""
         header = {"magic": CHECKPOINT_MAGIC, "dims": [32, 64, 64, 2], "params": N_PARAMS, "step": self.step}
         header.update(meta or {})
-        np.savez(path, params=self.params(), header=np.array(json.dumps(header)))
+        extra = {} if self.trust is None else {"trust": self.trust}
+        np.savez_compressed(path, params=self.params(), header=np.array(json.dumps(header)), **extra)
 
     @classmethod
     def from_checkpoint(cls, path, device="cuda"):
@@ -172,4 +200,6 @@ class Surrogate:
         s = cls(z["params"], device=device)
         s.step = int(header.get("step", 0))
         s.header = header
+        if "trust" in z.files:
+            s.set_trust(z["trust"])
         return s

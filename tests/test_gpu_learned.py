@@ -18,6 +18,7 @@ from oracle import mlp as omlp  # noqa: E402
 from oracle import rbsm as orc  # noqa: E402
 from tests import mlp_bounds as mb  # noqa: E402
 from tests.test_gpu_parity import dev  # noqa: E402
+from tests.window_rule import walks_inside_window  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -207,19 +208,20 @@ def test_training_lowers_the_loss_and_the_guard_trades_error_for_fallbacks(lib):
 
 
 def test_what_the_trained_network_gains(lib):
-    """On held-out edge fragments, with every surrogate answer accepted (no
-    guard), the trained network's mean error against the exact RSMSS answer
-    is well below that of the untrained network and below that of the hard
-    shadow test alone (the method without any penumbra estimate); the guard
-    (other tests) then sends the doubtful ones to the exact walk."""
+    """On held-out edge fragments whose walks stop inside the window (the
+    only ones the structural guard lets the network answer), with every
+    such answer accepted (no error-estimate guard), the trained network's
+    mean error against the exact RSMSS answer is well below that of the
+    untrained network and of the hard shadow test alone (the method without
+    any penumbra estimate)."""
     api, S = lib
     import rbsm_scenes as sc
     train = [sc.config2(s, screen=(1280, 720)) for s in (20, 21)]
     data = [(dev(f.depth), dev(f.x), dev(f.y), dev(f.z)) for f in train]
-    samples, count = S.Surrogate.dataset(data, capacity=1 << 20)
+    samples, count = S.Surrogate.dataset(data, capacity=1 << 20, in_window=True)
     untrained = S.Surrogate(sc.mlp_init(0))
     trained = S.Surrogate(sc.mlp_init(0))
-    trained.train(samples, count, epochs=4, batch=4096, lr=3e-3)
+    trained.train(samples, count, epochs=30, batch=1024, lr=3e-3, lr_decay=0.9)
     test = sc.config2(22, screen=(1280, 720))
     depth, x, y, z = dev(test.depth), dev(test.x), dev(test.y), dev(test.z)
 
@@ -232,16 +234,59 @@ def test_what_the_trained_network_gains(lib):
 
     exact, codes = run(None)
     edge = ((codes >> 9) & 1) == 1
-    assert edge.sum() > 1000
+    feat = orc.features(test.depth, test.x[edge], test.y[edge], test.z[edge])
+    inside = np.zeros_like(edge)
+    inside[edge] = walks_inside_window(feat["bits"])
+    assert inside.sum() > 1000
     hard = 1.0 - ((codes >> 4) & 1).astype(np.float64)          # the shadow test alone (1 = lit)
-    answers, answered = {}, edge.copy()
+    answers = {}
     for name, net in (("untrained", untrained), ("trained", trained)):
         f, c = run(net)
-        answered &= ((c >> 10) & 1) == 1                          # answered by the network
+        answered = ((c >> 10) & 1) == 1
+        assert np.array_equal(answered, inside)                   # the structural guard, fragment by fragment
         answers[name] = f
-    assert answered.sum() > 0.9 * edge.sum()
-    err = {name: np.abs(f[answered] - exact[answered]).mean() for name, f in answers.items()}
-    err["hard"] = np.abs(hard[answered] - exact[answered]).mean()
-    # measured on this scene: untrained 0.42, trained 0.12, hard 0.16
-    assert err["trained"] < 0.5 * err["untrained"], err
-    assert err["trained"] < 0.85 * err["hard"], err
+    err = {name: np.abs(f[inside] - exact[inside]).mean() for name, f in answers.items()}
+    err["hard"] = np.abs(hard[inside] - exact[inside]).mean()
+    assert err["trained"] < 0.3 * err["untrained"], err
+    assert err["trained"] < 0.3 * err["hard"], err
+
+
+# The surrogate's stated error bound: over the edge fragments it answers
+# with the committed checkpoint (its trusted-pattern bitmap in force) and
+# guard_tau = 0.01, the absolute error against the exact Listing 5 answer
+# has mean <= 0.01, 99th percentile <= 0.03 and maximum <= 0.1.  The bound
+# and tau were chosen on C2 seeds 12, 22, 31 and C4 seed 100 (largest error
+# 0.069); the scenes below served neither that nor training (C4 seeds
+# 0-114) nor calibration (C4 seeds 115-235).
+BOUND_TAU = 0.01
+BOUND = {"mean": 0.01, "p99": 0.03, "max": 0.1}
+
+
+@pytest.mark.parametrize("recipe", ["C2 seed 41", "C4 seed 102"])
+def test_surrogate_meets_its_stated_bound_on_held_out_scenes(lib, recipe):
+    api, S = lib
+    import os
+    import rbsm_scenes as sc
+    f = sc.config2(41) if recipe.startswith("C2") else sc.config4(102)
+    net = S.Surrogate.from_checkpoint(os.path.join(os.path.dirname(S.__file__), "weights", "surrogate_c4.npz"))
+    assert net.trust is not None
+    depth, x, y, z = dev(f.depth), dev(f.x), dev(f.y), dev(f.z)
+    job = api.Job(0, x, y, z, mode=2, codes=True)
+    b = api.Batch([depth], [job], surrogate=net, guard_tau=BOUND_TAU)
+    api.rbsm_batch_run(b)
+    torch.cuda.synchronize()
+    acc, fb = api.rbsm_batch_surrogate_counts(b)
+    codes = job.codes.cpu().numpy().view(np.uint16)
+    vis = job.vis_filter.cpu().numpy().astype(np.float64)
+    answered = ((codes >> 10) & 1) == 1
+    assert answered.sum() == acc > 10000
+    # judge: the oracle's Listing 5 answer of every answered fragment
+    ref = orc.evaluate(f.depth, f.x[answered], f.y[answered], f.z[answered], orc.MODE_FILTER)
+    assert np.all(((ref["codes"] >> 9) & 1) == 1)                  # only edge fragments are answered
+    feat = orc.features(f.depth, f.x[answered], f.y[answered], f.z[answered])
+    assert np.all(walks_inside_window(feat["bits"]))              # only inside-window ones
+    p = feat["bits"].astype(np.uint32)
+    assert np.all((net.trust[p >> 5] >> (p & 31)) & 1)            # only trusted patterns
+    err = np.abs(vis[answered] - ref["vis"])
+    got = {"mean": err.mean(), "p99": np.quantile(err, 0.99), "max": err.max()}
+    assert all(got[k] <= BOUND[k] for k in BOUND), (got, acc, fb)

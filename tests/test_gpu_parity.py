@@ -60,13 +60,12 @@ def assert_parity(vis, codes, ref, mode, where=""):
 
 def check_both(api, depth, x, y, z, where, max_dist=16, texture=False):
     """Both visibility modes against the oracle; with texture=True through a
-    texture view of the map as well (when the device accepts one)."""
+    texture view of the map as well (odd row pitches padded first)."""
     maps = [("loads", depth)]
     tex = None
     if texture:
-        tex = _try_texture(api, dev(depth))
-        if tex is not None:
-            maps.append(("texture", tex))
+        tex = _texture(api, dev(depth))
+        maps.append(("texture", tex))
     for mode in (orc.MODE_SILHOUETTE, orc.MODE_FILTER):
         ref = orc.evaluate(depth, x, y, z, mode, max_dist=max_dist)
         for name, d in maps:
@@ -218,13 +217,32 @@ def test_host_buffers_roundtrip(api):
     assert_parity(vis_h.numpy(), cod_h.numpy().view(np.uint16), ref, orc.MODE_FILTER, "host")
 
 
-def _try_texture(api, depth):
+TEX_PITCH_FLOATS = 128       # 512-byte rows: a multiple of any texture pitch alignment
+
+
+def _texture(api, depth):
+    """A texture view of the map (CUDA tensor).  A map whose rows are not a
+    multiple of 512 bytes is first copied into a buffer of 512-byte rows
+    (the view keeps its width), so every map size goes through the texture
+    path; creation must succeed."""
+    w = depth.shape[1]
+    if (depth.stride(0) * 4) % 512 != 0:
+        pitch = -(-w // TEX_PITCH_FLOATS) * TEX_PITCH_FLOATS
+        padded = torch.full((depth.shape[0], pitch), float("nan"), dtype=torch.float32, device=depth.device)
+        padded[:, :w] = depth
+        depth = padded[:, :w]
+    return api.MapTexture(depth)
+
+
+def test_texture_refused_only_for_unaligned_rows(api):
+    """rbsm_map_texture_create answers RBSM_ERR_ARG for rows that break the
+    device's pitch alignment, and nothing else."""
     from paper_1711_07793_gb300 import _native as N
-    try:
-        return api.MapTexture(depth)
-    except N.RBSMError as e:
-        assert e.code == N.RBSM_ERR_ARG
-        return None
+    buf = torch.zeros((16, 9), dtype=torch.float32, device="cuda")
+    with pytest.raises(N.RBSMError) as e:
+        api.MapTexture(buf)
+    assert e.value.code == N.RBSM_ERR_ARG
+    _texture(api, buf).close()
 
 
 @pytest.mark.parametrize("which", ["C1", "C2", "odd"])
@@ -246,9 +264,7 @@ def test_texture_gather_path(api, which):
             cases.append(_random_case(rng, w, h, 20000, spread=0.2))
     for depth, x, y, z in cases:
         d = dev(depth)
-        tex = _try_texture(api, d)
-        if tex is None:
-            continue
+        tex = _texture(api, d)
         for mode in (orc.MODE_SILHOUETTE, orc.MODE_FILTER):
             ref = orc.evaluate(depth, x, y, z, mode)
             vis, cod = run_gpu(api, tex, x, y, z, mode)
