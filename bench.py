@@ -57,6 +57,7 @@ def parse_args(argv=None):
     p.add_argument("--skip-light", action="store_true", help="profiling runs only")
     p.add_argument("--skip-gbuffer", action="store_true", help="profiling runs only")
     p.add_argument("--skip-sweep", action="store_true", help="profiling runs only")
+    p.add_argument("--only", default="", help="with --configs: comma-separated workloads (C1,C2,C3,C4)")
     p.add_argument("--configs", action="store_true",
                    help="one line per workload C1-C4 (GPU rate, roofline, oracle on 1 and all threads)")
     p.add_argument("--guard-tau", type=float, default=0.01, help="surrogate guard (largest accepted error estimate)")
@@ -808,7 +809,10 @@ def run_configs(args):
                  ("C2 2048^2, 1920x1080", lambda: [sc.config2(0)]),
                  ("C3 16 maps (512^2..4096^2) x 8 views (720p..4K), 4 lights", lambda: sc.Config3(0)),
                  ("C4 4096^2, 3840x2160", lambda: [sc.config4(0)])]
+    only = [o.strip().upper() for o in args.only.split(",") if o.strip()]
     for name, make in workloads:
+        if only and name.split()[0] not in only:
+            continue
         w = make()
         if isinstance(w, sc.Config3):
             maps_np = w.maps
@@ -822,7 +826,9 @@ def run_configs(args):
                   for k, x, y, z in parts]
         jobs = [api.Job(k, x, y, z, mode=3) for k, x, y, z in planes]
         batch = api.Batch(texs, jobs)
-        api.rbsm_batch_autotune(batch, repeats=3, cache=None)
+        tuning = None
+        if args.autotune == "on":
+            tuning = api.rbsm_batch_autotune(batch, repeats=3, cache=None)
         graph = api.BatchGraph(batch)
         for _ in range(5):
             graph.launch()
@@ -842,10 +848,13 @@ def run_configs(args):
         line = {"workload": name, "fragments": n, "unit": UNIT,
                 "gpu": {"value": n / (ms * 1e-3) / 1e9, "ms_per_launch": ms,
                         "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / peak, "peak_gbs": peak,
-                        "launch": {"tile_threads": batch.desc.tile_threads, "ctas_per_sm": batch.desc.ctas_per_sm}},
-                "cpu_oracle": {"threads_1": oracle_rate(cases, 1, 3.0),
-                               "threads_all": oracle_rate(cases, cores, 3.0), "cores": cores}}
-        if name.startswith("C4"):
+                        "launch": {"tile_threads": batch.desc.tile_threads, "ctas_per_sm": batch.desc.ctas_per_sm,
+                                   "chunk_tiles": batch.desc.chunk_tiles, "flags": batch.desc.flags},
+                        "autotune": tuning}}
+        if not args.skip_cpu:
+            line["cpu_oracle"] = {"threads_1": oracle_rate(cases, 1, 3.0),
+                                  "threads_all": oracle_rate(cases, cores, 3.0), "cores": cores}
+        if name.startswith("C4") and not args.skip_learned:
             line["learned"] = compare_learned(api, texs, [torch.stack([p[1], p[2], p[3]]) for p in planes],
                                               1, n, args, stream)
         graph.close()

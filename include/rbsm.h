@@ -252,7 +252,15 @@ typedef struct {
      * bit 10 set and no end counts (bits 5-9 clear). */
     const void *surrogate;
     float guard_tau;
+    int32_t chunk_tiles;           /* 128-fragment warp tiles a warp claims at a time from the
+                                    * work counter: 1, 2, 4 or 8; 0 = chosen from the batch size
+                                    * (8 when every warp gets about eight claims, halved below) */
+    int32_t flags;                 /* 0 or RBSM_BATCH_PLAIN_LOADS */
 } rbsm_batch;
+
+/* rbsm_batch.flags: read the four-neighbourhood with plain loads even where
+ * a map carries a texture (answers are the same bits either way). */
+#define RBSM_BATCH_PLAIN_LOADS 1
 
 /*
  * Device workspace a batch needs (a work counter and a status word), in
@@ -318,20 +326,27 @@ int rbsm_batch_graph_launch(rbsm_graph graph, void *stream);
 int rbsm_batch_graph_destroy(rbsm_graph graph);
 
 /*
- * Autotuner of the batched launch shape.  Times 7 candidate (CTA size,
- * CTAs per SM) pairs: 128 threads at its occupancy limit; 256 threads at 2,
- * 3, 4 and 5 (occupancy limit) CTAs per SM; 512 threads at 1 and 2.
- * Every warp works on its own 128-fragment tiles whatever the CTA size.
- * Each candidate gets `repeats` launches
- * each after one warm-up, on `stream`, and returns the fastest in *best.
- * It writes the batch's outputs (the answers stay correct) and waits for
- * the stream (cudaEventSynchronize): a set-up call, not for a frame loop.
+ * Autotuner of the batched launch.  Times every combination of
+ *   - 7 (CTA size, CTAs per SM) pairs: 128 threads at its occupancy limit;
+ *     256 threads at 2, 3, 4 and 5 (occupancy limit) CTAs per SM; 512
+ *     threads at 1 and 2;
+ *   - 4 claim sizes: 1, 2, 4 and 8 warp tiles per claim of the work counter;
+ *   - when any map carries a texture: texture gathers or plain loads for the
+ *     four-neighbourhood;
+ * with `repeats` launches each after one warm-up, on `stream`, and returns
+ * the fastest in *best (apply it through tile_threads, ctas_per_sm,
+ * chunk_tiles and flags).  Every warp works on its own 128-fragment tiles
+ * whatever the CTA size.  It writes the batch's outputs (the answers stay
+ * correct) and waits for the stream (cudaEventSynchronize): a set-up call,
+ * not for a frame loop.
  */
 typedef struct {
     int32_t tile_threads;
     int32_t ctas_per_sm;           /* 0 = occupancy limit */
     float ms;                      /* mean time per launch of the winner */
-    int32_t candidates;            /* shapes timed */
+    int32_t candidates;            /* combinations timed */
+    int32_t chunk_tiles;           /* claim size of the winner */
+    int32_t flags;                 /* RBSM_BATCH_PLAIN_LOADS when plain loads won */
 } rbsm_tuning;
 int rbsm_batch_autotune(const rbsm_batch *batch, void *workspace, size_t workspace_bytes, void *stream,
                         int32_t repeats, rbsm_tuning *best);

@@ -17,6 +17,7 @@ RBSM_ERR_ARG = -1
 RBSM_ERR_CUDA = -2
 RBSM_ERR_TIMEOUT = -3
 RBSM_DATASET_IN_WINDOW = 1
+RBSM_BATCH_PLAIN_LOADS = 1
 RBSM_MLP_TRUST_WORDS = 1 << 20
 RBSM_ERR_WORKSPACE = -4
 
@@ -54,7 +55,7 @@ class rbsm_batch(ctypes.Structure):
                 ("jobs", ctypes.POINTER(rbsm_job)), ("n_jobs", ctypes.c_int32),
                 ("params", rbsm_params), ("tile_threads", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("surrogate", ctypes.c_void_p),
-                ("guard_tau", ctypes.c_float)]
+                ("guard_tau", ctypes.c_float), ("chunk_tiles", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class rbsm_sample(ctypes.Structure):
@@ -67,7 +68,8 @@ RBSM_MLP_PARAMS = 6402
 
 class rbsm_tuning(ctypes.Structure):
     _fields_ = [("tile_threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("ms", ctypes.c_float), ("candidates", ctypes.c_int32)]
+                ("ms", ctypes.c_float), ("candidates", ctypes.c_int32), ("chunk_tiles", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
 
 
 class rbsm_stager_desc(ctypes.Structure):

@@ -184,7 +184,7 @@ class Batch:
     """Descriptor arrays of a batched launch, kept alive with their tensors."""
 
     def __init__(self, maps, jobs, max_dist=N.RBSM_MAXDIST_DEFAULT, tile_threads=0, ctas_per_sm=0,
-                 surrogate=None, guard_tau=0.0):
+                 surrogate=None, guard_tau=0.0, chunk_tiles=0, plain_loads=False):
         self.maps, self.jobs = list(maps), list(jobs)
         self.surrogate = surrogate
         self._maps = (N.rbsm_map * len(self.maps))(*[map_desc(m) for m in self.maps])
@@ -192,7 +192,8 @@ class Batch:
         self.desc = N.rbsm_batch(self._maps, len(self.maps), self._jobs, len(self.jobs),
                                  _params(max_dist), int(tile_threads), int(ctas_per_sm),
                                  surrogate.state.data_ptr() if surrogate is not None else None,
-                                 float(guard_tau))
+                                 float(guard_tau), int(chunk_tiles),
+                                 N.RBSM_BATCH_PLAIN_LOADS if plain_loads else 0)
         size = ctypes.c_size_t(0)
         N.check("rbsm_batch_workspace_size", N.lib().rbsm_batch_workspace_size(ctypes.byref(self.desc),
                                                                               ctypes.byref(size)))
@@ -201,9 +202,11 @@ class Batch:
         # 256-byte aligned: the caching allocator aligns blocks to 512 bytes
         self.workspace = torch.zeros(max(self.workspace_bytes, 256) // 4, dtype=torch.int32, device=dev)
 
-    def set_launch(self, tile_threads, ctas_per_sm):
+    def set_launch(self, tile_threads, ctas_per_sm, chunk_tiles=0, flags=0):
         self.desc.tile_threads = int(tile_threads)
         self.desc.ctas_per_sm = int(ctas_per_sm)
+        self.desc.chunk_tiles = int(chunk_tiles)
+        self.desc.flags = int(flags)
 
 
 def rbsm_batch_run(batch, stream=None):
@@ -255,7 +258,7 @@ def batch_signature(batch):
     name = torch.cuda.get_device_name(batch.jobs[0].x.device)
     maps = [tuple(m.depth.shape) + ("tex",) if isinstance(m, MapTexture) else tuple(m.shape) for m in batch.maps]
     jobs = [(j.map_index, j.mode, int(j.x.shape[0]), j.codes is not None) for j in batch.jobs]
-    return json.dumps([name, maps, jobs])
+    return json.dumps(["v2", name, maps, jobs])
 
 
 TUNE_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune_cache.json")
@@ -275,15 +278,17 @@ def rbsm_batch_autotune(batch, repeats=3, stream=None, cache=TUNE_CACHE):
             table = {}
     if key in table:
         hit = dict(table[key], cached=True)
-        batch.set_launch(hit["tile_threads"], hit["ctas_per_sm"])
+        batch.set_launch(hit["tile_threads"], hit["ctas_per_sm"], hit.get("chunk_tiles", 0), hit.get("flags", 0))
         return hit
     t = N.rbsm_tuning()
     N.check("rbsm_batch_autotune",
             N.lib().rbsm_batch_autotune(ctypes.byref(batch.desc), ctypes.c_void_p(batch.workspace.data_ptr()),
                                         batch.workspace_bytes, _stream_handle(stream), int(repeats),
                                         ctypes.byref(t)))
-    res = {"tile_threads": t.tile_threads, "ctas_per_sm": t.ctas_per_sm, "ms": t.ms, "candidates": t.candidates}
-    batch.set_launch(t.tile_threads, t.ctas_per_sm)
+    res = {"tile_threads": t.tile_threads, "ctas_per_sm": t.ctas_per_sm, "chunk_tiles": t.chunk_tiles,
+           "flags": t.flags, "plain_loads": bool(t.flags & N.RBSM_BATCH_PLAIN_LOADS), "ms": t.ms,
+           "candidates": t.candidates}
+    batch.set_launch(t.tile_threads, t.ctas_per_sm, t.chunk_tiles, t.flags)
     if cache:
         table[key] = res
         os.makedirs(os.path.dirname(cache), exist_ok=True)

@@ -75,7 +75,7 @@ BatchKernelFn kernel_for(int umode)
 }
 
 template <int kThreads, bool LEARNED, int kMinBlocks>
-int shape_for(const BatchArgs &args, int ctas_per_sm, int umode, LaunchShape *out)
+int shape_for(const BatchArgs &args, int ctas_per_sm, int chunk_req, int umode, LaunchShape *out)
 {
     const size_t smem = batch_smem_bytes<kThreads, LEARNED>();
     const BatchKernelFn fn = kernel_for<kThreads, LEARNED, kMinBlocks>(umode);
@@ -96,6 +96,8 @@ int shape_for(const BatchArgs &args, int ctas_per_sm, int umode, LaunchShape *ou
     int chunk = kMaxChunkTiles;
     while (chunk > 1 && args.total_tiles < 8LL * chunk * warps)
         chunk >>= 1;
+    if (chunk_req > 0)
+        chunk = chunk_req;
     const long long chunks = (args.total_tiles + chunk - 1) / chunk;
     const long long blocks_needed = (chunks + kThreads / 32 - 1) / (kThreads / 32);
     if (grid > blocks_needed)
@@ -121,24 +123,27 @@ int uniform_mode(const BatchArgs &a)
 // thread): asking for 3 selects the first, 5 or the occupancy limit (0) the
 // last, 1, 2 and 4 the middle one; the specialisations for a batch-uniform
 // mode exist for the 256-thread shapes.
-int launch_shape(const BatchArgs &args, int threads, int ctas_per_sm, LaunchShape *out)
+int launch_shape(const BatchArgs &args, int threads, int ctas_per_sm, int chunk, LaunchShape *out)
 {
+    if (chunk != 0 && chunk != 1 && chunk != 2 && chunk != 4 && chunk != kMaxChunkTiles)
+        return RBSM_ERR_ARG;
     const bool learned = args.mlp != nullptr;
     const int um = uniform_mode(args);
     if (learned) {
         switch (threads) {
-        case 128: return shape_for<128, true, 8>(args, ctas_per_sm, 0, out);
-        case 512: return shape_for<512, true, 2>(args, ctas_per_sm, 0, out);
-        default: return shape_for<256, true, 4>(args, ctas_per_sm, um, out);
+        case 128: return shape_for<128, true, 8>(args, ctas_per_sm, chunk, 0, out);
+        case 512: return shape_for<512, true, 2>(args, ctas_per_sm, chunk, 0, out);
+        default: return shape_for<256, true, 4>(args, ctas_per_sm, chunk, um, out);
         }
     }
     switch (threads) {
-    case 128: return shape_for<128, false, 8>(args, ctas_per_sm, 0, out);
-    case 512: return shape_for<512, false, 2>(args, ctas_per_sm, 0, out);
+    case 128: return shape_for<128, false, 8>(args, ctas_per_sm, chunk, 0, out);
+    case 512: return shape_for<512, false, 2>(args, ctas_per_sm, chunk, 0, out);
     default:
-        if (ctas_per_sm == 3) return shape_for<256, false, 3>(args, ctas_per_sm, um, out);
-        if (ctas_per_sm == 0 || ctas_per_sm >= 5) return shape_for<256, false, 5>(args, ctas_per_sm, um, out);
-        return shape_for<256, false, 4>(args, ctas_per_sm, um, out);
+        if (ctas_per_sm == 3) return shape_for<256, false, 3>(args, ctas_per_sm, chunk, um, out);
+        if (ctas_per_sm == 0 || ctas_per_sm >= 5)
+            return shape_for<256, false, 5>(args, ctas_per_sm, chunk, um, out);
+        return shape_for<256, false, 4>(args, ctas_per_sm, chunk, um, out);
     }
 }
 
@@ -163,6 +168,10 @@ int prepare_batch(const rbsm_batch *b, BatchArgs &a, int *threads)
         return RBSM_ERR_ARG;
     if (b->ctas_per_sm < 0 || b->ctas_per_sm > 8)
         return RBSM_ERR_ARG;
+    if ((b->chunk_tiles != 0 && b->chunk_tiles != 1 && b->chunk_tiles != 2 && b->chunk_tiles != 4 &&
+         b->chunk_tiles != kMaxChunkTiles) ||
+        (b->flags & ~RBSM_BATCH_PLAIN_LOADS))
+        return RBSM_ERR_ARG;
     int rc, max_dist;
     if ((rc = check_params(&b->params, &max_dist)) != RBSM_OK)
         return rc;
@@ -170,6 +179,8 @@ int prepare_batch(const rbsm_batch *b, BatchArgs &a, int *threads)
         if ((rc = check_map(&b->maps[k])) != RBSM_OK)
             return rc;
         a.maps[k] = to_dev(b->maps[k]);
+        if (b->flags & RBSM_BATCH_PLAIN_LOADS)
+            a.maps[k].tex = 0;
     }
     const long long tile = kWarpTile;
     long long tiles = 0;
@@ -280,7 +291,7 @@ int rbsm_batch_run(const rbsm_batch *batch, void *workspace, size_t workspace_by
     if (args.total_tiles == 0)
         return RBSM_OK;
     rbsm::LaunchShape sh;
-    if ((rc = rbsm::launch_shape(args, threads, batch->ctas_per_sm, &sh)) != RBSM_OK)
+    if ((rc = rbsm::launch_shape(args, threads, batch->ctas_per_sm, batch->chunk_tiles, &sh)) != RBSM_OK)
         return rc;
     return rbsm::enqueue_batch(args, sh, workspace, reinterpret_cast<cudaStream_t>(stream));
 }
@@ -300,7 +311,8 @@ int rbsm_batch_graph_create(const rbsm_batch *batch, void *workspace, size_t wor
         return rc;
     rbsm::bind_workspace(args, workspace);
     rbsm::LaunchShape sh{nullptr, 256, 1, 0, 1};
-    if (args.total_tiles > 0 && (rc = rbsm::launch_shape(args, threads, batch->ctas_per_sm, &sh)) != RBSM_OK)
+    if (args.total_tiles > 0 &&
+        (rc = rbsm::launch_shape(args, threads, batch->ctas_per_sm, batch->chunk_tiles, &sh)) != RBSM_OK)
         return rc;
     cudaStream_t s = nullptr;
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
@@ -374,6 +386,8 @@ int rbsm_batch_autotune(const rbsm_batch *batch, void *workspace, size_t workspa
     best->ctas_per_sm = 0;
     best->ms = -1.0f;
     best->candidates = 0;
+    best->chunk_tiles = 0;
+    best->flags = 0;
     if (args.total_tiles == 0)
         return RBSM_OK;
     cudaEvent_t t0, t1;
@@ -388,30 +402,45 @@ int rbsm_batch_autotune(const rbsm_batch *batch, void *workspace, size_t workspa
     // candidate (CTA size, CTAs per SM); 0 = the variant's occupancy limit
     const int cand[][2] = {{128, 0}, {256, 2}, {256, 3}, {256, 4}, {256, 0}, {512, 1}, {512, 0}};
     const int n_cand = (int)(sizeof(cand) / sizeof(cand[0]));
-    for (int ci = 0; ci < n_cand && rc == RBSM_OK; ++ci) {
-        {
-            rbsm::LaunchShape sh;
-            if ((rc = rbsm::launch_shape(args, cand[ci][0], cand[ci][1], &sh)) != RBSM_OK)
-                break;
-            if ((rc = rbsm::enqueue_batch(args, sh, workspace, s)) != RBSM_OK)   // warm-up
-                break;
-            if ((e = cudaEventRecord(t0, s)) != cudaSuccess) { rc = rbsm::cuda_fail(e); break; }
-            for (int r = 0; r < repeats && rc == RBSM_OK; ++r)
-                rc = rbsm::enqueue_batch(args, sh, workspace, s);
-            if (rc != RBSM_OK)
-                break;
-            if ((e = cudaEventRecord(t1, s)) != cudaSuccess || (e = cudaEventSynchronize(t1)) != cudaSuccess) {
-                rc = rbsm::cuda_fail(e);
-                break;
-            }
-            float ms = 0.0f;
-            if ((e = cudaEventElapsedTime(&ms, t0, t1)) != cudaSuccess) { rc = rbsm::cuda_fail(e); break; }
-            ms /= (float)repeats;
-            best->candidates += 1;
-            if (best->ms < 0.0f || ms < best->ms) {
-                best->ms = ms;
-                best->tile_threads = cand[ci][0];
-                best->ctas_per_sm = cand[ci][1];
+    const int chunks[] = {1, 2, 4, rbsm::kMaxChunkTiles};
+    // the maps' textures as given, and (when any map has one) plain loads
+    cudaTextureObject_t tex[RBSM_BATCH_MAX_MAPS];
+    bool any_tex = false;
+    for (int k = 0; k < batch->n_maps; ++k) {
+        tex[k] = args.maps[k].tex;
+        any_tex = any_tex || tex[k] != 0;
+    }
+    const int n_tex = any_tex ? 2 : 1;
+    for (int ti = 0; ti < n_tex && rc == RBSM_OK; ++ti) {
+        for (int k = 0; k < batch->n_maps; ++k)
+            args.maps[k].tex = ti == 0 ? tex[k] : 0;
+        for (int ci = 0; ci < n_cand && rc == RBSM_OK; ++ci) {
+            for (int ch = 0; ch < 4 && rc == RBSM_OK; ++ch) {
+                rbsm::LaunchShape sh;
+                if ((rc = rbsm::launch_shape(args, cand[ci][0], cand[ci][1], chunks[ch], &sh)) != RBSM_OK)
+                    break;
+                if ((rc = rbsm::enqueue_batch(args, sh, workspace, s)) != RBSM_OK)   // warm-up
+                    break;
+                if ((e = cudaEventRecord(t0, s)) != cudaSuccess) { rc = rbsm::cuda_fail(e); break; }
+                for (int r = 0; r < repeats && rc == RBSM_OK; ++r)
+                    rc = rbsm::enqueue_batch(args, sh, workspace, s);
+                if (rc != RBSM_OK)
+                    break;
+                if ((e = cudaEventRecord(t1, s)) != cudaSuccess || (e = cudaEventSynchronize(t1)) != cudaSuccess) {
+                    rc = rbsm::cuda_fail(e);
+                    break;
+                }
+                float ms = 0.0f;
+                if ((e = cudaEventElapsedTime(&ms, t0, t1)) != cudaSuccess) { rc = rbsm::cuda_fail(e); break; }
+                ms /= (float)repeats;
+                best->candidates += 1;
+                if (best->ms < 0.0f || ms < best->ms) {
+                    best->ms = ms;
+                    best->tile_threads = cand[ci][0];
+                    best->ctas_per_sm = cand[ci][1];
+                    best->chunk_tiles = chunks[ch];
+                    best->flags = ti == 0 ? (batch->flags & RBSM_BATCH_PLAIN_LOADS) : RBSM_BATCH_PLAIN_LOADS;
+                }
             }
         }
     }
@@ -509,7 +538,7 @@ extern "C" int rbsm_batch_run_noalloc(const rbsm_batch *batch, void *stream)
     if (args.total_tiles == 0)
         return RBSM_OK;
     rbsm::LaunchShape sh;
-    if ((rc = rbsm::launch_shape(args, threads, batch->ctas_per_sm, &sh)) != RBSM_OK)
+    if ((rc = rbsm::launch_shape(args, threads, batch->ctas_per_sm, batch->chunk_tiles, &sh)) != RBSM_OK)
         return rc;
     // enqueue_batch clears the counters that must start at zero (a memset of
     // the array's first 32 bytes, stream-ordered before the kernel)

@@ -25,8 +25,9 @@ struct LaunchShape {
 // Validate a batch and fill the kernel arguments (everything but the
 // workspace pointers).  Returns RBSM_OK or RBSM_ERR_ARG.
 int prepare_batch(const rbsm_batch *b, BatchArgs &a, int *threads);
-// Kernel variant, grid and shared memory for a prepared batch.
-int launch_shape(const BatchArgs &args, int threads, int ctas_per_sm, LaunchShape *out);
+// Kernel variant, grid and shared memory for a prepared batch; chunk = warp
+// tiles per claim (1, 2, 4, 8), 0 = chosen from the batch size.
+int launch_shape(const BatchArgs &args, int threads, int ctas_per_sm, int chunk, LaunchShape *out);
 int check_workspace(const void *ws, size_t bytes);
 // Point the kernel arguments at the counter, status word and statistics of
 // a workspace.

@@ -315,7 +315,7 @@ int run_map(rbsm_stager_s *st, const rbsm_batch *b, int map_index, const int *id
         return rc;
     bind_workspace(args, s.ws);
     LaunchShape sh;
-    if ((rc = launch_shape(args, threads, db.ctas_per_sm, &sh)) != RBSM_OK)
+    if ((rc = launch_shape(args, threads, db.ctas_per_sm, db.chunk_tiles, &sh)) != RBSM_OK)
         return rc;
     RBSM_CK(cudaStreamWaitEvent(st->s_cmp, s.in_done, 0));
     if ((rc = enqueue_batch(args, sh, s.ws, st->s_cmp)) != RBSM_OK)

@@ -53,6 +53,8 @@ int main(void) {
          offsetof(rbsm_occluders, zscale), offsetof(rbsm_occluders, flags));
   printf("%zu %zu %zu %zu\n", sizeof(rbsm_gbuffer), offsetof(rbsm_gbuffer, m), sizeof(rbsm_gbuffer_job),
          offsetof(rbsm_gbuffer_job, vis_filter));
+  printf("%zu %zu %zu %zu %zu\n", offsetof(rbsm_batch, chunk_tiles), offsetof(rbsm_batch, flags),
+         sizeof(rbsm_tuning), offsetof(rbsm_tuning, chunk_tiles), offsetof(rbsm_tuning, flags));
   return 0;
 }
 ''')
@@ -72,6 +74,9 @@ int main(void) {
     oc = [int(v) for v in lines[3].split()]
     assert oc == [N.RBSM_RECT_BYTES, N.RBSM_SPHERE_BYTES, ctypes.sizeof(N.rbsm_occluders),
                   N.rbsm_occluders.zscale.offset, N.rbsm_occluders.flags.offset]
+    bt = [int(v) for v in lines[5].split()]
+    assert bt == [N.rbsm_batch.chunk_tiles.offset, N.rbsm_batch.flags.offset, ctypes.sizeof(N.rbsm_tuning),
+                  N.rbsm_tuning.chunk_tiles.offset, N.rbsm_tuning.flags.offset]
     st = [int(v) for v in lines[2].split()]
     assert st == [ctypes.sizeof(N.rbsm_stager_desc), N.rbsm_stager_desc.max_width.offset,
                   N.rbsm_stager_desc.slots.offset, N.rbsm_stager_desc.flags.offset]
@@ -121,6 +126,9 @@ def test_bad_arguments_are_rejected_before_any_cuda_call(native):
     assert lib.rbsm_batch_run(B(N.rbsm_batch(maps, 1, jobs, 0, p, 0, 0)), addr, 4096, None) == N.RBSM_ERR_ARG
     assert lib.rbsm_batch_run(B(N.rbsm_batch(maps, 1, jobs, 1, p, 192, 0)), addr, 4096, None) == N.RBSM_ERR_ARG
     assert lib.rbsm_batch_run(B(N.rbsm_batch(maps, 65, jobs, 1, p, 0, 0)), addr, 4096, None) == N.RBSM_ERR_ARG
+    for chunk, flags in ((3, 0), (16, 0), (-1, 0), (0, 2)):
+        bad = N.rbsm_batch(maps, 1, jobs, 1, p, 0, 0, None, 0.0, chunk, flags)
+        assert lib.rbsm_batch_run(B(bad), addr, 4096, None) == N.RBSM_ERR_ARG
     # the stager: descriptors are checked before any CUDA call
     h = ctypes.c_void_p(0)
     for bad in (N.rbsm_stager_desc(0, 64, 64, 0, 0, 0), N.rbsm_stager_desc(10, 0, 64, 0, 0, 0),

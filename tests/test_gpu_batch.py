@@ -32,8 +32,8 @@ def small_c3():
     return sc.Config3(seed=1, views=[(320, 180), (256, 144), (200, 130)], cascades=[1024, 512, 256], lights=2)
 
 
-def _batch(api, scene, modes, codes=True, **kw):
-    maps = [dev(m) for m in scene.maps]
+def _batch(api, scene, modes, codes=True, maps=None, **kw):
+    maps = maps if maps is not None else [dev(m) for m in scene.maps]
     jobs = []
     for k, j in enumerate(scene.jobs):
         mode = modes[k % len(modes)]
@@ -74,15 +74,24 @@ def test_batch_matches_oracle(api, small_c3):
 @pytest.mark.parametrize("threads", [128, 256, 512])
 @pytest.mark.parametrize("ctas", [0, 1, 3, 4, 5])
 def test_every_launch_shape_gives_the_same_answers(api, small_c3, threads, ctas):
+    """Every candidate of the autotuner (CTA size, CTAs per SM, claim size,
+    texture gathers or plain loads) gives the bits of the default launch."""
     ref = _batch(api, small_c3, modes=[3], codes=False)
     api.rbsm_batch_run(ref)
-    b = _batch(api, small_c3, modes=[3], codes=False, tile_threads=threads, ctas_per_sm=ctas)
-    api.rbsm_batch_run(b)
-    api.rbsm_batch_run(b)          # a second launch reuses the workspace
     torch.cuda.synchronize()
-    for j, r in zip(b.jobs, ref.jobs):
-        assert torch.equal(j.vis_silhouette, r.vis_silhouette)
-        assert torch.equal(j.vis_filter, r.vis_filter)
+    texs = [api.MapTexture(dev(m)) for m in small_c3.maps]
+    for chunk in (1, 2, 4, 8):
+        for maps, plain in ((None, False), (texs, False), (texs, True)):
+            b = _batch(api, small_c3, modes=[3], codes=False, tile_threads=threads, ctas_per_sm=ctas,
+                       chunk_tiles=chunk, plain_loads=plain, maps=maps)
+            api.rbsm_batch_run(b)
+            api.rbsm_batch_run(b)          # a second launch reuses the workspace
+            torch.cuda.synchronize()
+            for j, r in zip(b.jobs, ref.jobs):
+                assert torch.equal(j.vis_silhouette, r.vis_silhouette), (chunk, plain, maps is None)
+                assert torch.equal(j.vis_filter, r.vis_filter), (chunk, plain, maps is None)
+    for t in texs:
+        t.close()
 
 
 def test_batch_with_empty_and_tiny_jobs(api):
@@ -138,12 +147,26 @@ def test_graph_replay_and_autotune(api, small_c3, tmp_path):
     g.close()
     cache = str(tmp_path / "tune.json")
     t = api.rbsm_batch_autotune(b, repeats=2, cache=cache)
-    assert t["candidates"] == 7 and t["tile_threads"] in (128, 256, 512) and not t["cached"]
-    assert api.rbsm_batch_autotune(b, cache=cache)["cached"]
+    # 7 (CTA size, CTAs per SM) pairs x 4 claim sizes; no map has a texture
+    assert t["candidates"] == 28 and t["tile_threads"] in (128, 256, 512) and not t["cached"]
+    assert t["chunk_tiles"] in (1, 2, 4, 8) and not t["plain_loads"]
+    hit = api.rbsm_batch_autotune(b, cache=cache)
+    assert hit["cached"] and b.desc.chunk_tiles == t["chunk_tiles"]
     api.rbsm_batch_run(b)
     torch.cuda.synchronize()
     for j, r in zip(b.jobs, ref.jobs):
         assert torch.equal(j.vis_filter, r.vis_filter)
+    # with map textures the tuner also weighs plain loads against the gathers
+    texs = [api.MapTexture(dev(m)) for m in small_c3.maps]
+    bt = _batch(api, small_c3, modes=[3], codes=True, maps=texs)
+    tt = api.rbsm_batch_autotune(bt, repeats=1, cache=None)
+    assert tt["candidates"] == 56
+    api.rbsm_batch_run(bt)
+    torch.cuda.synchronize()
+    for j, r in zip(bt.jobs, ref.jobs):
+        assert torch.equal(j.vis_filter, r.vis_filter) and torch.equal(j.codes, r.codes)
+    for x in texs:
+        x.close()
 
 
 def test_batch_with_textures_matches_plain_loads(api, small_c3):
