@@ -726,7 +726,7 @@ def measure_maxdist(api, maps, xyz, frames, n_frag, args, stream, shape, caps=(8
     closed-form ramp on staircase edges of run lengths 8..64."""
     import numpy as np
     import torch
-    from tests import shapes
+    from rbsm_scenes import shapes
     n = 512
     offs = [((a + 0.5) / 16, (b + 0.5) / 16) for a in range(16) for b in range(16)]
     stairs = []

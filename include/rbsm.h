@@ -309,6 +309,12 @@ int rbsm_batch_run(const rbsm_batch *batch, void *workspace, size_t workspace_by
 #define RBSM_NOALLOC_SCRATCH_BYTES 256
 int rbsm_batch_run_noalloc(const rbsm_batch *batch, void *stream);
 
+/* The surrogate counters (as rbsm_batch_surrogate_counts) of the last
+ * rbsm_batch_run_noalloc launch on the current device, read from the
+ * library's array once the stream has completed it (synchronous
+ * device-to-host copy); RBSM_ERR_CUDA when no call has run on the device. */
+int rbsm_batch_noalloc_counts(uint64_t *accepted, uint64_t *fallback);
+
 /*
  * CUDA graph of one batched launch (the workspace memset and the persistent
  * kernel), built once and replayed with one cudaGraphLaunch per frame.  The
@@ -360,8 +366,10 @@ int rbsm_batch_surrogate_counts(const void *workspace, uint64_t *accepted, uint6
 
 /*
  * After the stream has completed a batch: read its device status word
- * (synchronously, with a device-to-host copy) and return RBSM_OK or the
- * RBSM_ERR_* code the kernel recorded.
+ * (synchronously, with a device-to-host copy) into *status.  The word is
+ * cleared before every launch and reserved: the batched kernel has no wait
+ * and no condition to record (every argument is checked on the host before
+ * the launch), so it reads RBSM_OK.
  */
 int rbsm_batch_status(const void *workspace, int *status);
 

@@ -142,6 +142,8 @@ def _declare(lib):
     lib.rbsm_batch_run.argtypes = [_P(rbsm_batch), vp, ctypes.c_size_t, vp]
     lib.rbsm_batch_run_noalloc.restype = i32
     lib.rbsm_batch_run_noalloc.argtypes = [_P(rbsm_batch), vp]
+    lib.rbsm_batch_noalloc_counts.restype = i32
+    lib.rbsm_batch_noalloc_counts.argtypes = [_P(ctypes.c_uint64), _P(ctypes.c_uint64)]
     lib.rbsm_batch_graph_create.restype = i32
     lib.rbsm_batch_graph_create.argtypes = [_P(rbsm_batch), vp, ctypes.c_size_t, _P(vp)]
     lib.rbsm_batch_graph_launch.restype = i32

@@ -544,3 +544,22 @@ extern "C" int rbsm_batch_run_noalloc(const rbsm_batch *batch, void *stream)
     // the array's first 32 bytes, stream-ordered before the kernel)
     return rbsm::enqueue_batch(args, sh, scratch, reinterpret_cast<cudaStream_t>(stream));
 }
+
+extern "C" int rbsm_batch_noalloc_counts(uint64_t *accepted, uint64_t *fallback)
+{
+    if (!accepted || !fallback)
+        return RBSM_ERR_ARG;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return rbsm::cuda_fail(e);
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (dev >= 0 && dev < rbsm::KernelSetup::kMaxDevices)
+            scratch = g_noalloc_ptr[dev];
+    }
+    if (!scratch)
+        return rbsm::cuda_fail(cudaErrorInvalidResourceHandle);   // no call has run on this device
+    return rbsm_batch_surrogate_counts(scratch, accepted, fallback);
+}

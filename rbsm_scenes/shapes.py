@@ -1,4 +1,5 @@
-"""Hand-built shadow maps and fragment grids for the pins (test inputs only).
+"""Hand-built shadow maps and fragment grids: the pins' inputs and the bench's
+staircase sweep.
 
 Nothing here computes any step of the method: these helpers only place
 occluder texels and fragment positions, and apply the eight symmetries of the

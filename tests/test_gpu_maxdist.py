@@ -12,7 +12,7 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-from tests import shapes  # noqa: E402
+from rbsm_scenes import shapes  # noqa: E402
 
 
 @pytest.fixture(scope="module")

@@ -13,7 +13,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from oracle import rbsm as orc  # noqa: E402
-from tests import shapes  # noqa: E402
+from rbsm_scenes import shapes  # noqa: E402
 
 FILTER_TOL = 1e-5
 

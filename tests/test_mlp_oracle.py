@@ -12,7 +12,7 @@ import pytest
 
 from oracle import mlp
 from oracle import rbsm as orc
-from tests import shapes
+from rbsm_scenes import shapes
 
 
 def test_bf16_round_is_nearest_even():

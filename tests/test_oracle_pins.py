@@ -19,7 +19,7 @@ import numpy as np
 import pytest
 
 from oracle import rbsm as orc
-from tests import shapes
+from rbsm_scenes import shapes
 
 SIL, FIL = orc.MODE_SILHOUETTE, orc.MODE_FILTER
 

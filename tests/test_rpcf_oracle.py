@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 from oracle import rbsm as orc
-from tests import shapes
+from rbsm_scenes import shapes
 
 
 def test_k1_is_rsmss():
