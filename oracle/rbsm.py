@@ -42,6 +42,8 @@ def _load():
             ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
             ctypes.c_double, ctypes.c_float]
+        lib.oracle_edge_visibility.restype = ctypes.c_double
+        lib.oracle_edge_visibility.argtypes = [ctypes.c_int32] * 6 + [ctypes.c_double, ctypes.c_double]
         lib.oracle_features.restype = ctypes.c_int
         lib.oracle_features.argtypes = [
             ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
@@ -159,3 +161,11 @@ def features(depth, x, y, z):
     if rc != 0:
         raise ValueError("oracle_features rejected its arguments (rc=%d)" % rc)
     return {"bits": bits, "fx": fx, "fy": fy, "gap": gap}
+
+
+def edge_visibility(mode, opposite_x, opposite_y, ends_x, ends_y, dz, nx, ny):
+    """The oracle's visibility of an edge fragment from its shape inputs
+    (§4: discontinuity directions on both sides of each axis, ends found
+    along each axis, dz = 1 - shadow test, normalised distances)."""
+    return _load().oracle_edge_visibility(int(mode), int(opposite_x), int(opposite_y), int(ends_x), int(ends_y),
+                                          int(dz), float(nx), float(ny))

@@ -170,42 +170,84 @@ static float axis_position_f32(int r_neg, int r_pos, float f)
     return r_neg > 0 ? from_neg : from_pos;
 }
 
-/* Listing 4, §4.1: silhouette recovery for a lit edge fragment.
- * dxq, dyq are the compressed discontinuities of Eq. 4 in quarters
- * (3 = 0.75 = edges on both sides of the axis); cx, cy the Eq. 5 codes. */
-static double silhouette_visibility(int dxq, int dyq, int cx, int cy, float nx, float ny)
+/* The four shadow-edge shapes of Fig. 2 (§3.1.4, §3.2.4, §4), told apart
+ * from what the fragment's neighbourhood and traversal found: per axis,
+ * whether the fragment has discontinuity directions on both sides
+ * (opposite[a]: d.x or d.y of Eq. 4 is 0.75) and how many of the two walks
+ * along it found an end (ends[a] = 0, 1, 2; Eq. 5 codes them 1, 0, -1 for
+ * 2, 1, 0). */
+enum { SHAPE_I, SHAPE_L, SHAPE_U, SHAPE_O };
+
+/* §4.1, silhouette recovery: U- and O-shaped edges are those with
+ * discontinuity directions on both sides of an axis or an end found on both
+ * sides of an axis (the fragment sits between two shadowed neighbours); an
+ * I-shaped edge is one where no end was found along an axis; every other
+ * edge is L-shaped.  (U and O get the same answer.) */
+static int silhouette_shape(const int opposite[2], const int ends[2])
 {
-    if (dxq == 3 || dyq == 3)      /* short U or O shape */
-        return 0.0;
-    if (cx == 1 || cy == 1)        /* long U or O shape */
-        return 0.0;
-    if (cx == -1 || cy == -1)      /* I shape */
-        return 1.0;
-    /* L shape: shadow below the revectorisation line ny = 1 - nx, a point on
-     * the line stays lit */
-    float line = 1.0f - nx;
-    return ny < line ? 0.0 : 1.0;
+    for (int a = 0; a < 2; ++a)
+        if (opposite[a] || ends[a] == 2)
+            return SHAPE_U;
+    for (int a = 0; a < 2; ++a)
+        if (ends[a] == 0)
+            return SHAPE_I;
+    return SHAPE_L;
 }
 
-/* Listing 5, §4.2: filtering (fake penumbra) for an edge fragment on either
- * side of the edge; dz = 1 - s.  R11 for the I-shape test. */
-static double filter_visibility(int dxq, int dyq, int dz, int cx, int cy, double nx, double ny)
+/* §4.1: U and O edges are closed (shadow), I edges stay as the shadow test
+ * found them (lit: only lit fragments get here), and an L edge is cut by
+ * the revectorisation line through the corner of the aliasing: a fragment
+ * is shadowed when its vertical distance ny is below 1 - its horizontal
+ * distance nx (float32, as the shader computes it; a point on the line
+ * stays lit). */
+static double silhouette_visibility(const int opposite[2], const int ends[2], float nx, float ny)
 {
-    double sgn = 1.0 - 2.0 * (double)dz;
-    if (dxq == 3 && dyq == 3)      /* short O shape: close it */
-        return (double)dz;
-    if (cx == 1 && cy == 1)        /* long O shape */
-        return (double)dz;
-    if (cx == 1)                   /* U shape open along y */
-        return (double)dz + sgn * ny;
-    if (cy == 1)                   /* U shape open along x */
-        return (double)dz + sgn * nx;
-    if (cx == -1 || cy == -1)      /* I shape: the plain shadow test */
-        return 1.0 - (double)dz;
-    double v = (double)dz + sgn * ny + sgn * nx;   /* L shape */
-    if (v < 0.0) v = 0.0;
-    if (v > 1.0) v = 1.0;
-    return v;
+    switch (silhouette_shape(opposite, ends)) {
+    case SHAPE_U: return 0.0;
+    case SHAPE_I: return 1.0;
+    default: {
+        float line = 1.0f - nx;
+        return ny < line ? 0.0 : 1.0;
+    }
+    }
+}
+
+/* §4.2, filtering: an O-shaped edge is closed on both axes (discontinuity
+ * directions on both sides of both axes, or ends on both sides of both);
+ * a U-shaped edge has ends on both sides of one axis; an I-shaped edge has
+ * no end along an axis; every other edge is L-shaped. */
+static int filter_shape(const int opposite[2], const int ends[2])
+{
+    if ((opposite[0] && opposite[1]) || (ends[0] == 2 && ends[1] == 2))
+        return SHAPE_O;
+    if (ends[0] == 2 || ends[1] == 2)
+        return SHAPE_U;
+    if (ends[0] == 0 || ends[1] == 0)      /* R11 */
+        return SHAPE_I;
+    return SHAPE_L;
+}
+
+/* §4.2, on either side of the edge (dz = 1 - s, sign = 1 - 2 dz):
+ *   O: the opposite of the shadow test (the edge is closed);
+ *   U: the normalised distance across the open axis, measured from the
+ *      fragment's side (ends along x: ny; ends along y: nx);
+ *   I: the shadow test;
+ *   L: the sum of both normalised distances from the fragment's side,
+ *      clamped to [0, 1]. */
+static double filter_visibility(const int opposite[2], const int ends[2], int dz, double nx, double ny)
+{
+    const double sgn = 1.0 - 2.0 * (double)dz;
+    switch (filter_shape(opposite, ends)) {
+    case SHAPE_O: return (double)dz;
+    case SHAPE_U: return ends[0] == 2 ? (double)dz + sgn * ny : (double)dz + sgn * nx;
+    case SHAPE_I: return 1.0 - (double)dz;
+    default: {
+        double v = (double)dz + sgn * ny + sgn * nx;
+        if (v < 0.0) v = 0.0;
+        if (v > 1.0) v = 1.0;
+        return v;
+    }
+    }
 }
 
 /* Listing 1 with Listings 2-5: visibility of one fragment.
@@ -259,12 +301,14 @@ static void rbsm_fragment_uv(const sm_t *sm, float u, float v, float pz, int mod
         int ex = (rd[0] > 0) + (rd[1] > 0);
         int ey = (rd[2] > 0) + (rd[3] > 0);
         code = (uint16_t)(code | (ex << 5) | (ey << 7) | (1 << 9));
+        const int opposite[2] = {dxq == 3, dyq == 3};
+        const int ends[2] = {ex, ey};
         if (mode == ORACLE_MODE_SILHOUETTE) {
             float nx32 = axis_position_f32(rd[0], rd[1], fx);
             float ny32 = axis_position_f32(rd[2], rd[3], fy);
-            vis = silhouette_visibility(dxq, dyq, cx, cy, nx32, ny32);
+            vis = silhouette_visibility(opposite, ends, nx32, ny32);
         } else {
-            vis = filter_visibility(dxq, dyq, dz, cx, cy, nx, ny);
+            vis = filter_visibility(opposite, ends, dz, nx, ny);
         }
     }
     *vis_out = vis;
@@ -283,6 +327,20 @@ static void rbsm_fragment(const sm_t *sm, float x, float y, float pz, int mode, 
     float u = x * (float)sm->width;
     float v = y * (float)sm->height;
     rbsm_fragment_uv(sm, u, v, pz, mode, max_dist, vis_out, code_out, rd_out, nrd_out);
+}
+
+/* The visibility of an edge fragment from its shape inputs alone (per axis:
+ * discontinuity directions on both sides, ends found; dz; the normalised
+ * distances), for the tests that set it against the listings' branches.
+ * Silhouette mode takes nx, ny as float32, as the fragment path does. */
+double oracle_edge_visibility(int32_t mode, int32_t opposite_x, int32_t opposite_y, int32_t ends_x,
+                              int32_t ends_y, int32_t dz, double nx, double ny)
+{
+    const int opposite[2] = {opposite_x != 0, opposite_y != 0};
+    const int ends[2] = {ends_x, ends_y};
+    if (mode == ORACLE_MODE_SILHOUETTE)
+        return silhouette_visibility(opposite, ends, (float)nx, (float)ny);
+    return filter_visibility(opposite, ends, dz, nx, ny);
 }
 
 /* Evaluate n fragments.  Returns 0, or -1 on invalid arguments.
