@@ -92,11 +92,11 @@ struct LearnedSmem {
 };
 
 // Drain rounds of up to 32 queued edge fragments with the surrogate: each
-// lane gathers its fragment's 5x5 features into one input row, the warp runs
-// the network on the 32 rows (two m16 tiles on the tensor cores), and each
-// fragment whose walks stop inside the window, whose pattern is trusted and
-// whose error estimate is within the guard takes the estimate, clamped to
-// [0, 1]; the others (and every fragment of a job that is not in FILTER
+// lane gathers its fragment's 5x5 features; the fragments whose walks stop
+// inside the window and whose pattern is trusted are packed into input rows
+// and the warp runs the network on as many m16 tiles as they fill (0, 1 or
+// 2, on the tensor cores); each of them whose error estimate is within the
+// guard takes the estimate, clamped to [0, 1]; the others (and every fragment of a job that is not in FILTER
 // mode) go to the warp's fallback queue, whose exact walks run in
 // rounds of 32 like the exact path's (walked in place, a round's few
 // fallbacks would keep most lanes idle through the walk).
@@ -136,22 +136,23 @@ __device__ __forceinline__ void drain_queue_learned(const Jobs &jobs, WarpQueue 
             o = jobs((int)(q.bits_job >> 8));
         }
         const bool use_net = valid && o.mode == 2;
-        bool in_window = false;
+        // the structural guard and the trusted-pattern bitmap need only the
+        // window pattern: fragments they turn down skip the network, and
+        // the others are packed into the first rows of the round
+        bool eligible = false;
+        uint32_t bits = 0;
+        float fx = 0.0f, fy = 0.0f, gap = 0.0f;
         if (use_net) {
-            uint32_t bits;
-            float fx, fy, gap;
             fragment_features(o.map, __ldg(o.x + q.idx), __ldg(o.y + q.idx), __ldg(o.z + q.idx), bits, fx, fy, gap);
-            in_window = walks_inside_window(bits, max_dist) && mlp::pattern_trusted(ls.trust, bits);
-            mlp::write_input_row(feat + lane * mlp::kIn, bits, fx, fy, gap);
-        } else {
-            uint4 *row = reinterpret_cast<uint4 *>(feat + lane * mlp::kIn);
-#pragma unroll
-            for (int w4 = 0; w4 < mlp::kIn / 8; ++w4)
-                row[w4] = make_uint4(0u, 0u, 0u, 0u);
+            eligible = walks_inside_window(bits, max_dist) && mlp::pattern_trusted(ls.trust, bits);
         }
+        const unsigned elig_mask = __ballot_sync(0xffffffffu, eligible);
+        const int row = __popc(elig_mask & below);
+        if (eligible)
+            mlp::write_input_row(feat + row * mlp::kIn, bits, fx, fy, gap);
         __syncwarp();
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
+        const int tiles = (__popc(elig_mask) + 15) >> 4;     // m16 tiles with rows in use (0..2)
+        for (int mt = 0; mt < tiles; ++mt) {
             uint32_t xa[2][4];
             mlp::load_a(feat, mlp::kIn, mt * 16, 0, lane, xa[0]);
             mlp::load_a(feat, mlp::kIn, mt * 16, 1, lane, xa[1]);
@@ -170,19 +171,16 @@ __device__ __forceinline__ void drain_queue_learned(const Jobs &jobs, WarpQueue 
         }
         __syncwarp();
         bool accepted = false;
-        if (use_net) {
-            const float v = yout[lane * 2], e = yout[lane * 2 + 1];
-            // structural guard: the answer must be a function of what the
-            // network sees, and its pattern trusted by calibration (when a
-            // bitmap is in force); then the network's own error estimate (a
-            // NaN never passes)
-            accepted = in_window && e <= tau && v == v;
+        if (eligible) {
+            const float v = yout[row * 2], e = yout[row * 2 + 1];
+            // the network's own error estimate (a NaN never passes)
+            accepted = e <= tau && v == v;
             if (accepted) {
                 const float vc = v < 0.0f ? 0.0f : (v > 1.0f ? 1.0f : v);
                 o.fil[q.idx] = vc;
                 if (o.codes) {
-                    const uint32_t bits = q.bits_job & 0x1fu;
-                    o.codes[q.idx] = (uint16_t)((bits >> 1) | ((1u - (bits & 1u)) << 4) | (1u << 10));
+                    const uint32_t cb = q.bits_job & 0x1fu;
+                    o.codes[q.idx] = (uint16_t)((cb >> 1) | ((1u - (cb & 1u)) << 4) | (1u << 10));
                 }
             }
         }
