@@ -257,30 +257,32 @@ struct FragResult {
 };
 
 // Steps 1-2 from the five depths of the texel and its neighbours.
+// (The tests stay predicates: a neighbour's discontinuity is its test
+// differing from the centre's, and the answer is selected, not converted.)
 template <int MODE, bool CODES>
 __device__ __forceinline__ bool classify_from(float pz, float zc, float zl, float zr, float zu, float zd,
                                               FragResult &r, uint32_t &bits)
 {
-    const int s0 = shadow_test(pz, zc);
-    if (MODE == 1 && !CODES && s0 == 0) {
+    const bool shadowed = pz > zc;             // Eq. 1: s0 = 0
+    if (MODE == 1 && !CODES && shadowed) {
         r.sil = 0.0f;
         r.code = 0;
         bits = 0;
         return false;
     }
-    const uint32_t dl = shadow_test(pz, zl) != s0;
-    const uint32_t dr = shadow_test(pz, zr) != s0;
-    const uint32_t du = shadow_test(pz, zu) != s0;
-    const uint32_t dd = shadow_test(pz, zd) != s0;
+    const uint32_t dl = (pz > zl) != shadowed;
+    const uint32_t dr = (pz > zr) != shadowed;
+    const uint32_t du = (pz > zu) != shadowed;
+    const uint32_t dd = (pz > zd) != shadowed;
     const uint32_t d4 = dl | (dr << 1) | (du << 2) | (dd << 3);
-    bits = (uint32_t)s0 | (d4 << 1);
-    r.code = (uint16_t)(d4 | ((1 - s0) << 4));
-    const float sv = (float)s0;
+    bits = (shadowed ? 0u : 1u) | (d4 << 1);
+    r.code = (uint16_t)(d4 | (shadowed ? 16u : 0u));
+    const float sv = shadowed ? 0.0f : 1.0f;
     r.sil = sv;
     r.fil = sv;
     const bool edge = d4 != 0;
     if (MODE == 1)
-        return edge && s0 == 1;
+        return edge && !shadowed;
     return edge;
 }
 
@@ -315,10 +317,9 @@ __device__ __forceinline__ bool classify_uv(const MapDev &m, float u, float v, f
     texel_of(v, m.height, j, fy);
     const float *c = m.depth + (long long)j * m.pitch + i;
     const float zc = __ldg(c);
-    const int s0 = shadow_test(pz, zc);
     // Listing 1: in silhouette recovery a shadowed fragment stays shadowed and
     // needs no neighbourhood (unless codes are requested).
-    if (MODE == 1 && !CODES && s0 == 0) {
+    if (MODE == 1 && !CODES && pz > zc) {
         r.sil = 0.0f;
         r.code = 0;
         bits = 0;
@@ -328,24 +329,7 @@ __device__ __forceinline__ bool classify_uv(const MapDev &m, float u, float v, f
     const long long dn = j > 0 ? m.pitch : 0;
     const int lf = i > 0 ? 1 : 0;
     const int rt = i < m.width - 1 ? 1 : 0;
-    const float zl = __ldg(c - lf);
-    const float zr = __ldg(c + rt);
-    const float zu = __ldg(c + up);
-    const float zd = __ldg(c - dn);
-    const uint32_t dl = shadow_test(pz, zl) != s0;
-    const uint32_t dr = shadow_test(pz, zr) != s0;
-    const uint32_t du = shadow_test(pz, zu) != s0;
-    const uint32_t dd = shadow_test(pz, zd) != s0;
-    const uint32_t d4 = dl | (dr << 1) | (du << 2) | (dd << 3);
-    bits = (uint32_t)s0 | (d4 << 1);
-    r.code = (uint16_t)(d4 | ((1 - s0) << 4));
-    const float sv = (float)s0;
-    r.sil = sv;
-    r.fil = sv;
-    const bool edge = d4 != 0;
-    if (MODE == 1)
-        return edge && s0 == 1;
-    return edge;
+    return classify_from<MODE, CODES>(pz, zc, __ldg(c - lf), __ldg(c + rt), __ldg(c + up), __ldg(c - dn), r, bits);
 }
 
 // Steps 1-2 from a texture coordinate (u = x * W, v = y * H in float32).
