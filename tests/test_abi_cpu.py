@@ -106,6 +106,26 @@ def test_bad_arguments_are_rejected_before_any_cuda_call(native):
         assert fn(B(good_map), B(good_frags), addr, None, B(N.rbsm_params(16, 1)), None) == N.RBSM_ERR_ARG
         # n == 0 enqueues nothing and succeeds without touching the device
         assert fn(B(good_map), B(N.rbsm_frags(None, None, None, 0)), None, None, None, None) == N.RBSM_OK
+    # the surrogate's training and set-up calls (a 256-byte aligned state is required)
+    big = (ctypes.c_float * 1024)()
+    state = (ctypes.addressof(big) + 255) & ~255
+    assert lib.rbsm_mlp_step(None, addr, addr, 8, 1, ctypes.c_float(1e-3), None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_mlp_step(state + 4, addr, addr, 8, 1, ctypes.c_float(1e-3), None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_mlp_step(state, None, addr, 8, 1, ctypes.c_float(1e-3), None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_mlp_step(state, addr, addr, 0, 1, ctypes.c_float(1e-3), None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_mlp_step(state, addr, addr, 8, 0, ctypes.c_float(1e-3), None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_mlp_step(state, addr, addr, 8, 1, ctypes.c_float(0.0), None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_mlp_grad(state, addr, None, 8, None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_mlp_grad(state + 16, addr, addr, 8, None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_mlp_forward(state + 16, addr, 4, addr, None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_mlp_forward(state, None, 4, addr, None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_mlp_forward(state, addr, 0, None, None) == N.RBSM_OK
+    assert lib.rbsm_mlp_set_trust(None, None, None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_mlp_set_trust(state + 8, None, None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_batch_noalloc_counts(None, None) == N.RBSM_ERR_ARG
+    bad_flags = N.rbsm_params(16, 2)
+    counter = (ctypes.c_uint64 * 1)()
+    assert lib.rbsm_mlp_dataset(B(good_map), B(good_frags), B(bad_flags), addr, 4, counter, None) == N.RBSM_ERR_ARG
     for k in (0, 2, 9, -3):
         assert lib.rbsm_rpcf(B(good_map), B(good_frags), addr, k, B(p), None) == N.RBSM_ERR_ARG
     assert lib.rbsm_rpcf(None, B(good_frags), addr, 3, B(p), None) == N.RBSM_ERR_ARG
