@@ -491,6 +491,35 @@ __device__ __forceinline__ void fetch_tile(const WarpTileIO &t, unsigned lane, c
     }
 }
 
+// The same with lane l holding fragments l, l + 32, l + 64, l + 96 for
+// vector tiles too (the scalar tiles' order): the staged planes are read
+// back transposed, so a warp's lanes hold consecutive fragments at each
+// element.  Consecutive fragments fall on the same or neighbouring texels,
+// so one gather instruction of the warp touches a few cache lines instead
+// of a strip four fragments apart per lane.  The buffer is read by other
+// lanes than the one that copied it: a warp barrier after the wait, and
+// another before the buffer is refilled.
+__device__ __forceinline__ void fetch_tile_strided(const WarpTileIO &t, unsigned lane, const float4 (&buf)[3][32],
+                                                   LaneCoords &c)
+{
+    if (t.vec) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncwarp();
+        const float *bx = reinterpret_cast<const float *>(buf[0]);
+        const float *by = reinterpret_cast<const float *>(buf[1]);
+        const float *bz = reinterpret_cast<const float *>(buf[2]);
+#pragma unroll
+        for (int e = 0; e < kPerThread; ++e) {
+            c.x[e] = bx[lane + 32 * e];
+            c.y[e] = by[lane + 32 * e];
+            c.z[e] = bz[lane + 32 * e];
+        }
+        __syncwarp();
+    } else {
+        load_tile(t, lane, c);
+    }
+}
+
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 // Walk, normalise and answer one deferred edge fragment; write its answers.

@@ -51,8 +51,9 @@ __device__ __forceinline__ uint32_t to_fix(float v)
 // up to the next integer where it crosses a power of two) and the (K + 2)^2
 // block of texels around floor(u), floor(v) lies inside the map (no
 // clamping), all K^2 samples' four-neighbourhoods come from that one block:
-// ceil((K + 2) / 2)^2 texture gathers instead of 2 K^2, and one shadow test
-// (Eq. 1) per texel.  Other fragments take the per-sample path.
+// 7 texture gathers for k = 3 and ceil((K + 2) / 2)^2 for larger k instead
+// of 2 K^2, and one shadow test (Eq. 1) per texel.  Other fragments take the
+// per-sample path.
 template <int K>
 __device__ __forceinline__ bool block_ok(float u, float v, float uhi, float vhi)
 {
@@ -67,10 +68,27 @@ __device__ __forceinline__ bool block_ok(float u, float v, float uhi, float vhi)
     return ok;
 }
 
+// Shadow tests (Eq. 1) of the four texels of the gather at block columns
+// p, p + 1 and rows q, q + 1 into the row masks.  A gather at (X, Y) covers
+// columns X - 1, X and rows Y - 1, Y; components x = (lo col, hi row),
+// y = (hi, hi), z = (hi, lo), w = (lo, lo).
+template <int K>
+__device__ __forceinline__ void gather_bits(const MapDev &m, float gx, float gy, int p, int q, float pz,
+                                            uint32_t (&rows)[K + 2])
+{
+    const float4 g = tex2Dgather<float4>(m.tex, gx + (float)p, gy + (float)q, 0);
+    rows[q] |= ((uint32_t)!(pz > g.w) << p) | ((uint32_t)!(pz > g.z) << (p + 1));
+    if (q + 1 < K + 2)
+        rows[q + 1] |= ((uint32_t)!(pz > g.x) << p) | ((uint32_t)!(pz > g.y) << (p + 1));
+}
+
 // Bit x of rows[y]: texel (floor(u) - R - 1 + x, floor(v) - R - 1 + y) is
-// lit for depth pz (Eq. 1).  Gather (X, Y) covers columns X - 1, X and rows
-// Y - 1, Y; components x = (lo col, hi row), y = (hi, hi), z = (hi, lo),
-// w = (lo, lo).
+// lit for depth pz (Eq. 1).  The samples' classification reads the block
+// without its four corners (each sample's texel and its four neighbours).
+// For k = 3 that is 21 texels of the 5 x 5 block, which seven gathers cover
+// (rows 0-1 at columns 0-3, rows 3-4 at columns 1-4, and three across the
+// middle row); larger k take the whole block, ceil((K + 2) / 2)^2 gathers.
+// Bits of the corners may be missing; nothing reads them.
 template <int K>
 __device__ __forceinline__ void block_bits(const MapDev &m, float u, float v, float pz, uint32_t (&rows)[K + 2])
 {
@@ -79,14 +97,20 @@ __device__ __forceinline__ void block_bits(const MapDev &m, float u, float v, fl
 #pragma unroll
     for (int y = 0; y < B; ++y)
         rows[y] = 0u;
+    if constexpr (K == 3) {
+        gather_bits<K>(m, gx, gy, 0, 0, pz, rows);
+        gather_bits<K>(m, gx, gy, 2, 0, pz, rows);
+        gather_bits<K>(m, gx, gy, 3, 1, pz, rows);
+        gather_bits<K>(m, gx, gy, 1, 1, pz, rows);
+        gather_bits<K>(m, gx, gy, 0, 2, pz, rows);
+        gather_bits<K>(m, gx, gy, 1, 3, pz, rows);
+        gather_bits<K>(m, gx, gy, 3, 3, pz, rows);
+    } else {
 #pragma unroll
-    for (int n = 0; n < G; ++n) {
+        for (int n = 0; n < G; ++n) {
 #pragma unroll
-        for (int c = 0; c < G; ++c) {
-            const float4 g = tex2Dgather<float4>(m.tex, gx + (float)(2 * c), gy + (float)(2 * n), 0);
-            rows[2 * n] |= ((uint32_t)!(pz > g.w) << (2 * c)) | ((uint32_t)!(pz > g.z) << (2 * c + 1));
-            if (2 * n + 1 < B)
-                rows[2 * n + 1] |= ((uint32_t)!(pz > g.x) << (2 * c)) | ((uint32_t)!(pz > g.y) << (2 * c + 1));
+            for (int c = 0; c < G; ++c)
+                gather_bits<K>(m, gx, gy, 2 * c, 2 * n, pz, rows);
         }
     }
 }
@@ -160,14 +184,14 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
         const bool more = nt < tiles;
         WarpTileIO tn;
         LaneCoords c;
-        fetch_tile(t, lane, buf, c);
+        fetch_tile_strided(t, lane, buf, c);
         if (more) {
             tn = io_of(nt);
             stage_tile(tn, lane, buf);     // next tile's copies fly during this tile
         }
 #pragma unroll 1
         for (int e = 0; e < kPerThread; ++e) {
-            const int s = t.vec ? (int)(kPerThread * lane) + e : (int)lane + 32 * e;
+            const int s = (int)lane + 32 * e;
             const bool valid = s < t.count;
             const float xe = e == 0 ? c.x[0] : e == 1 ? c.x[1] : e == 2 ? c.x[2] : c.x[3];
             const float ye = e == 0 ? c.y[0] : e == 1 ? c.y[1] : e == 2 ? c.y[2] : c.y[3];
