@@ -140,6 +140,134 @@ __device__ __forceinline__ void walks_y(const MapDev &m, int i, int j, float pz,
     walk_pair(col, col_l, col_r, m.pitch, j, m.height - 1, left, right, pz, s0, max_dist, rn, rp);
 }
 
+// Walks through the map's texture view, S steps per iteration (S even).
+// A 2x2 gather returns two consecutive texels of the walk's line and of one
+// neighbouring line, so an iteration takes S steps of a direction with S/2
+// gathers per side line in use (one side: S/2, both: S).  The texture
+// clamps to the edge as the scalar walk clamps its indices, so every step
+// reads the texels walk_pair reads; steps past an end or past max_dist are
+// fetched but not tested.  Gather order: x = (lo col, hi row), y = (hi, hi),
+// z = (hi, lo), w = (lo, lo); a gather at (X, Y) covers columns X-1, X and
+// rows Y-1, Y.  Used by RPCF, whose drains it speeds up (k = 3 / 5:
+// 39.6 -> 40.5, 17.7 -> 19.4 Gfrag/s); the batched kernel keeps the scalar
+// walk (C5 0.351 vs 0.385 ms on 8 frames, C4 94 vs 107 us per frame).
+
+template <int S>
+__device__ __forceinline__ void walk_steps(const float (&zl)[S], const float (&za)[S], const float (&zb)[S],
+                                           bool use_a, bool use_b, float pz, int s0, int k, int max_dist, int &r)
+{
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        if (r == 0 && k + t <= max_dist) {
+            if (shadow_test(pz, zl[t]) != s0)
+                r = k + t;
+            else if (!((use_a && shadow_test(pz, za[t]) != s0) || (use_b && shadow_test(pz, zb[t]) != s0)))
+                r = -(k + t);
+        }
+    }
+}
+
+// Along x from texel (i, j): line row j, sides rows j+1 (up) and j-1 (down).
+template <int S>
+__device__ __forceinline__ void walks_x_tex(const MapDev &m, int i, int j, float pz, int s0, bool up, bool down,
+                                            int max_dist, int &rn, int &rp)
+{
+    rn = 0;
+    rp = 0;
+    const float fj = (float)j;
+    const bool hi_pair = up || !down;      // the line from the rows j, j+1 gather unless only j-1 is in use
+    for (int k = 1; k <= max_dist; k += S) {
+        const bool on = rn == 0, op = rp == 0;
+        float ln[S], la[S], lb[S], lp[S], pa[S], pb[S];
+#pragma unroll
+        for (int g = 0; g < S / 2; ++g) {
+            // +x: columns i+k+2g (lo, step k+2g) and i+k+2g+1 (hi)
+            const float xp = (float)(i + k + 2 * g + 1);
+            float4 pu = make_float4(0.0f, 0.0f, 0.0f, 0.0f), pd = pu;
+            if (op && hi_pair)
+                pu = tex2Dgather<float4>(m.tex, xp, fj + 1.0f, 0);
+            if (op && down)
+                pd = tex2Dgather<float4>(m.tex, xp, fj, 0);
+            lp[2 * g] = hi_pair ? pu.w : pd.x;
+            lp[2 * g + 1] = hi_pair ? pu.z : pd.y;
+            pa[2 * g] = pu.x;
+            pa[2 * g + 1] = pu.y;
+            pb[2 * g] = pd.w;
+            pb[2 * g + 1] = pd.z;
+            // -x: columns i-k-2g (hi, step k+2g) and i-k-2g-1 (lo)
+            const float xn = (float)(i - k - 2 * g);
+            float4 nu = make_float4(0.0f, 0.0f, 0.0f, 0.0f), nd = nu;
+            if (on && hi_pair)
+                nu = tex2Dgather<float4>(m.tex, xn, fj + 1.0f, 0);
+            if (on && down)
+                nd = tex2Dgather<float4>(m.tex, xn, fj, 0);
+            ln[2 * g] = hi_pair ? nu.z : nd.y;
+            ln[2 * g + 1] = hi_pair ? nu.w : nd.x;
+            la[2 * g] = nu.y;
+            la[2 * g + 1] = nu.x;
+            lb[2 * g] = nd.z;
+            lb[2 * g + 1] = nd.w;
+        }
+        walk_steps<S>(ln, la, lb, up, down, pz, s0, k, max_dist, rn);
+        walk_steps<S>(lp, pa, pb, up, down, pz, s0, k, max_dist, rp);
+        if (rn != 0 && rp != 0)
+            break;
+    }
+    rn = rn == 0 ? -(max_dist + 1) : rn;
+    rp = rp == 0 ? -(max_dist + 1) : rp;
+}
+
+// Along y from texel (i, j): line column i, sides columns i-1 (left) and
+// i+1 (right).
+template <int S>
+__device__ __forceinline__ void walks_y_tex(const MapDev &m, int i, int j, float pz, int s0, bool left, bool right,
+                                            int max_dist, int &rn, int &rp)
+{
+    rn = 0;
+    rp = 0;
+    const float fi = (float)i;
+    const bool lo_pair = left || !right;   // the line from the columns i-1, i gather unless only i+1 is in use
+    for (int k = 1; k <= max_dist; k += S) {
+        const bool on = rn == 0, op = rp == 0;
+        float ln[S], la[S], lb[S], lp[S], pa[S], pb[S];
+#pragma unroll
+        for (int g = 0; g < S / 2; ++g) {
+            // +y: rows j+k+2g (lo, step k+2g) and j+k+2g+1 (hi)
+            const float yp = (float)(j + k + 2 * g + 1);
+            float4 pl = make_float4(0.0f, 0.0f, 0.0f, 0.0f), pr = pl;
+            if (op && lo_pair)
+                pl = tex2Dgather<float4>(m.tex, fi, yp, 0);
+            if (op && right)
+                pr = tex2Dgather<float4>(m.tex, fi + 1.0f, yp, 0);
+            lp[2 * g] = lo_pair ? pl.z : pr.w;
+            lp[2 * g + 1] = lo_pair ? pl.y : pr.x;
+            pa[2 * g] = pl.w;
+            pa[2 * g + 1] = pl.x;
+            pb[2 * g] = pr.z;
+            pb[2 * g + 1] = pr.y;
+            // -y: rows j-k-2g (hi, step k+2g) and j-k-2g-1 (lo)
+            const float yn = (float)(j - k - 2 * g);
+            float4 nl = make_float4(0.0f, 0.0f, 0.0f, 0.0f), nr = nl;
+            if (on && lo_pair)
+                nl = tex2Dgather<float4>(m.tex, fi, yn, 0);
+            if (on && right)
+                nr = tex2Dgather<float4>(m.tex, fi + 1.0f, yn, 0);
+            ln[2 * g] = lo_pair ? nl.y : nr.x;
+            ln[2 * g + 1] = lo_pair ? nl.z : nr.w;
+            la[2 * g] = nl.x;
+            la[2 * g + 1] = nl.w;
+            lb[2 * g] = nr.y;
+            lb[2 * g + 1] = nr.z;
+        }
+        walk_steps<S>(ln, la, lb, left, right, pz, s0, k, max_dist, rn);
+        walk_steps<S>(lp, pa, pb, left, right, pz, s0, k, max_dist, rp);
+        if (rn != 0 && rp != 0)
+            break;
+    }
+    rn = rn == 0 ? -(max_dist + 1) : rn;
+    rp = rp == 0 ? -(max_dist + 1) : rp;
+}
+
 // Eq. 5 and the normalisation along one axis: the position of the fragment
 // measured from the end that was found, over the length of the aliased edge
 // along that axis (|r_neg| + |r_pos| - 1 texels).  With no end found the
@@ -341,8 +469,9 @@ __device__ __forceinline__ bool classify(const MapDev &m, float x, float y, floa
 }
 
 // Steps 3-4 for one edge fragment at texel-space position (u, v)
-// (recomputes its texel).
-template <int MODE>
+// (recomputes its texel).  TEX_STEPS > 0: walk through the map's texture
+// view (when it has one), TEX_STEPS steps per iteration.
+template <int MODE, int TEX_STEPS = 0>
 __device__ __forceinline__ void resolve_edge_uv(const MapDev &m, float u, float v, float pz,
                                                 uint32_t bits, int max_dist, FragResult &r)
 {
@@ -353,11 +482,19 @@ __device__ __forceinline__ void resolve_edge_uv(const MapDev &m, float u, float 
     int s0 = bits & 1;
     bool dl = (bits >> 1) & 1, dr = (bits >> 2) & 1, du = (bits >> 3) & 1, dd = (bits >> 4) & 1;
     // computeFragmentDistanceToSE: the four walks -x, +x, -y, +y
-    // (with a texture view too: 2x2 gathers that take two steps per fetch
-    // measured slower than these loads)
     int rxn, rxp, ryn, ryp;
-    walks_x(m, i, j, pz, s0, du, dd, max_dist, rxn, rxp);
-    walks_y(m, i, j, pz, s0, dl, dr, max_dist, ryn, ryp);
+    bool done = false;
+    if constexpr (TEX_STEPS > 0) {
+        if (m.tex) {
+            walks_x_tex<TEX_STEPS>(m, i, j, pz, s0, du, dd, max_dist, rxn, rxp);
+            walks_y_tex<TEX_STEPS>(m, i, j, pz, s0, dl, dr, max_dist, ryn, ryp);
+            done = true;
+        }
+    }
+    if (!done) {
+        walks_x(m, i, j, pz, s0, du, dd, max_dist, rxn, rxp);
+        walks_y(m, i, j, pz, s0, dl, dr, max_dist, ryn, ryp);
+    }
     int ex = (rxn > 0) + (rxp > 0);
     int ey = (ryn > 0) + (ryp > 0);
     float nx = axis_position(rxn, rxp, fx);
