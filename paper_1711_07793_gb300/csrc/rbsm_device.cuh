@@ -72,31 +72,44 @@ __device__ __forceinline__ void texel_coord(float x, int size, int &t, float &f)
 // walk towards higher ones.
 //
 // The walks read three fixed lines of the map (the row or column of the
-// fragment and its two neighbours): `line` points at the first texel of the
-// fragment's own line, `side_a`/`side_b` at the neighbouring lines that
-// share a direction (use_a/use_b), `stride` is the distance between
-// consecutive texels of a line and `pos`/`last` the fragment's index and the
-// last index along it.  The two directions advance together and every load
-// of a step (of both walks; a finished walk issues none) is in flight before
-// the first test, so a step costs one memory latency.  Loads of later steps
-// are not issued ahead: the extra, mostly wasted, requests cost more than
-// the latency they hide.
-__device__ __forceinline__ void walk_pair(const float *line, const float *side_a, const float *side_b,
-                                          long long stride, int pos, int last, bool use_a, bool use_b,
-                                          float pz, int s0, int max_dist, int &rn, int &rp)
+// fragment and its two neighbours).  `line` points at the first texel of
+// the fragment's own line, `stride` is the distance between consecutive
+// texels of a line, `pos`/`last` the fragment's index and the last index
+// along it; each direction steps a pointer along the line and holds it at
+// the border (clamp to edge).  The side lines that share a direction
+// (use_a/use_b) lie da and db elements from the line; with kAdjacent (the
+// walks along y) they are the columns i-1 and i+1, read at the immediate
+// offsets -1 and +1.  A side is only read when the fragment has a
+// discontinuity towards it, and at the map border the clamped neighbour is
+// the texel itself and shows none, so a side that is read exists and the
+// offsets never leave the map.  The two directions advance together and
+// every load of a step (of both walks; a finished walk issues none) is in
+// flight before the first test, so a step costs one memory latency.  Loads
+// of later steps are not issued ahead: the extra, mostly wasted, requests
+// cost more than the latency they hide.
+template <bool kAdjacent>
+__device__ __forceinline__ void walk_pair(const float *line, long long da, long long db, long long stride,
+                                          int pos, int last, bool use_a, bool use_b, float pz, int s0,
+                                          int max_dist, int &rn, int &rp)
 {
     rn = 0;
     rp = 0;
+    const float *pn = line + (long long)pos * stride;
+    const float *pp = pn;
+    const int room_n = pos, room_p = last - pos;
+    const long long oa = kAdjacent ? -1 : da, ob = kAdjacent ? 1 : db;
     for (int k = 1; k <= max_dist; ++k) {
         const bool an = rn == 0, ap = rp == 0;
-        const long long offn = (long long)max(pos - k, 0) * stride;
-        const long long offp = (long long)min(pos + k, last) * stride;
-        const float zcn = an ? __ldg(line + offn) : 0.0f;
-        const float zan = an && use_a ? __ldg(side_a + offn) : 0.0f;
-        const float zbn = an && use_b ? __ldg(side_b + offn) : 0.0f;
-        const float zcp = ap ? __ldg(line + offp) : 0.0f;
-        const float zap = ap && use_a ? __ldg(side_a + offp) : 0.0f;
-        const float zbp = ap && use_b ? __ldg(side_b + offp) : 0.0f;
+        if (k <= room_n)
+            pn -= stride;
+        if (k <= room_p)
+            pp += stride;
+        const float zcn = an ? __ldg(pn) : 0.0f;
+        const float zan = an && use_a ? __ldg(pn + oa) : 0.0f;
+        const float zbn = an && use_b ? __ldg(pn + ob) : 0.0f;
+        const float zcp = ap ? __ldg(pp) : 0.0f;
+        const float zap = ap && use_a ? __ldg(pp + oa) : 0.0f;
+        const float zbp = ap && use_b ? __ldg(pp + ob) : 0.0f;
         if (an) {
             if (shadow_test(pz, zcn) != s0)
                 rn = k;
@@ -124,9 +137,8 @@ __device__ __forceinline__ void walks_x(const MapDev &m, int i, int j, float pz,
                                         bool up, bool down, int max_dist, int &rn, int &rp)
 {
     const float *row = m.depth + (long long)j * m.pitch;
-    const float *row_up = m.depth + (long long)min(j + 1, m.height - 1) * m.pitch;
-    const float *row_dn = m.depth + (long long)max(j - 1, 0) * m.pitch;
-    walk_pair(row, row_up, row_dn, 1, i, m.width - 1, up, down, pz, s0, max_dist, rn, rp);
+    const long long du = j < m.height - 1 ? m.pitch : 0, dd = j > 0 ? -m.pitch : 0;
+    walk_pair<false>(row, du, dd, 1, i, m.width - 1, up, down, pz, s0, max_dist, rn, rp);
 }
 
 // The walks along y from texel (i, j): columns i, i-1 (shared left) and i+1
@@ -134,10 +146,7 @@ __device__ __forceinline__ void walks_x(const MapDev &m, int i, int j, float pz,
 __device__ __forceinline__ void walks_y(const MapDev &m, int i, int j, float pz, int s0,
                                         bool left, bool right, int max_dist, int &rn, int &rp)
 {
-    const float *col = m.depth + i;
-    const float *col_l = m.depth + max(i - 1, 0);
-    const float *col_r = m.depth + min(i + 1, m.width - 1);
-    walk_pair(col, col_l, col_r, m.pitch, j, m.height - 1, left, right, pz, s0, max_dist, rn, rp);
+    walk_pair<true>(m.depth + i, 0, 0, m.pitch, j, m.height - 1, left, right, pz, s0, max_dist, rn, rp);
 }
 
 // Walks through the map's texture view, S steps per iteration (S even).
