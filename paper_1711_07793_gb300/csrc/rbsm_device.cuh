@@ -157,9 +157,11 @@ __device__ __forceinline__ void walks_y(const MapDev &m, int i, int j, float pz,
 // reads the texels walk_pair reads; steps past an end or past max_dist are
 // fetched but not tested.  Gather order: x = (lo col, hi row), y = (hi, hi),
 // z = (hi, lo), w = (lo, lo); a gather at (X, Y) covers columns X-1, X and
-// rows Y-1, Y.  Used by RPCF, whose drains it speeds up (k = 3 / 5:
-// 39.6 -> 40.5, 17.7 -> 19.4 Gfrag/s); the batched kernel keeps the scalar
-// walk (C5 0.351 vs 0.385 ms on 8 frames, C4 94 vs 107 us per frame).
+// rows Y-1, Y.  Used by RPCF for k != 3, whose drains it speeds up (against
+// the scalar walk stepping one pointer per direction: k = 1 / 7 at 128.4 /
+// 11.1 against 124.1 / 10.9 Gfrag/s, k = 3 at 40.25 against 40.6); the
+// batched kernel keeps the scalar walk (C5 0.351 vs 0.385 ms on 8 frames,
+// C4 94 vs 107 us per frame, measured against the earlier scalar walk).
 
 template <int S>
 __device__ __forceinline__ void walk_steps(const float (&zl)[S], const float (&za)[S], const float (&zb)[S],

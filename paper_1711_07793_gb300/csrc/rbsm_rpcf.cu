@@ -163,7 +163,9 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
                 FragResult r;
                 uint32_t bits;
                 classify_uv<2, false>(m, ua, vb, pz, r, bits);    // the sample's discontinuity again
-                resolve_edge_uv<2, 2>(m, ua, vb, pz, bits, max_dist, r);    // walks through the texture view
+                // walks through the texture view (two steps per gather), except
+                // for k = 3, where the scalar walk measured 1 % faster
+                resolve_edge_uv<2, K == 3 ? 0 : 2>(m, ua, vb, pz, bits, max_dist, r);
                 if (K == 1)
                     vis[i] = r.fil;
                 else if (r.fil != r.fil)
