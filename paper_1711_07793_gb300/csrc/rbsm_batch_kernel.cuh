@@ -80,11 +80,12 @@ struct BatchJobs {
     }
 };
 
-// Shared memory of the learned variant: the network's weights and, per
-// warp, the 32 input rows and 32 outputs of one round of edge fragments.
+// Shared memory of the learned variant: the network's biases and weight
+// pointers and, per warp, the 32 input rows and 32 outputs of one round of
+// edge fragments.
 template <int kThreads>
 struct LearnedSmem {
-    mlp::SmemWeights w;
+    mlp::InferWeights w;
     uint16_t feat[kThreads / 32][32 * mlp::kIn];
     float out[kThreads / 32][32 * mlp::kOut];
     EdgeEntry fallback[kThreads / 32][64];      // guard-tripped fragments: < 32 left over + one round
@@ -161,7 +162,7 @@ __device__ __forceinline__ void drain_queue_learned(const Jobs &jobs, WarpQueue 
             mlp::layer(xa, 2, ls.w.w1t, mlp::kIn, ls.w.b1, lane, h1, m1);
             mlp::layer(h1.a, 4, ls.w.w2t, mlp::kHid, ls.w.b2, lane, h2, m2);
             float y[4];
-            mlp::output_layer(h2, ls.w, lane, y);
+            mlp::output_layer(h2, ls.w.w3t, ls.w.b3, lane, y);
             if (t == 0) {
                 yout[(mt * 16 + g) * 2] = y[0];
                 yout[(mt * 16 + g) * 2 + 1] = y[1];
@@ -242,9 +243,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const __gri
     const int warp = threadIdx.x >> 5;
     if (LEARNED) {
         const mlp::State st = mlp::state_of(const_cast<void *>(a.mlp));
-        for (int k = threadIdx.x; k < mlp::kW1tElems; k += kThreads) ls.w.w1t[k] = st.w1t[k];
-        for (int k = threadIdx.x; k < mlp::kW2tElems; k += kThreads) ls.w.w2t[k] = st.w2t[k];
-        for (int k = threadIdx.x; k < mlp::kW3tElems; k += kThreads) ls.w.w3t[k] = st.w3t[k];
+        if (threadIdx.x == 0) {
+            ls.w.w1t = st.w1t;
+            ls.w.w2t = st.w2t;
+            ls.w.w3t = st.w3t;
+        }
         for (int k = threadIdx.x; k < mlp::kHid; k += kThreads) {
             ls.w.b1[k] = st.master[mlp::kOffB1 + k];
             ls.w.b2[k] = st.master[mlp::kOffB2 + k];
