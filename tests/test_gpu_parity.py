@@ -157,6 +157,25 @@ def test_out_of_range_and_nan_coordinates(api):
     check_both(api, depth, x, y, z, "out-of-range")
 
 
+def test_border_texels(api):
+    """Fragments on every texel of the first and last rows and columns of
+    random two-level maps, whose edges run along and across the borders: a
+    walk there reads its side lines only towards neighbours inside the map
+    (a clamped neighbour is the texel itself and shows no discontinuity), and
+    the answers and codes match the oracle on plain loads and textures."""
+    rng = np.random.default_rng(11)
+    for w, h in ((64, 48), (7, 5), (2, 33)):
+        depth = np.where(rng.random((h, w)) < 0.5, 0.3, 0.9).astype(np.float32)
+        cols = np.concatenate([np.arange(w), np.arange(w), np.zeros(h, int), np.full(h, w - 1)])
+        rows = np.concatenate([np.zeros(w, int), np.full(w, h - 1), np.arange(h), np.arange(h)])
+        offs = [(0.25, 0.25), (0.75, 0.5), (0.5, 0.9)]
+        x = np.concatenate([(cols + fx) / w for fx, _ in offs]).astype(np.float32)
+        y = np.concatenate([(rows + fy) / h for _, fy in offs]).astype(np.float32)
+        z = np.full(x.shape, 0.6, np.float32)
+        for md in (2, 16):
+            check_both(api, depth, x, y, z, "border %dx%d max_dist=%d" % (w, h, md), max_dist=md, texture=True)
+
+
 @pytest.mark.parametrize("max_dist", [1, 2, 3, 5, 16, 17, 64, 255])
 def test_max_dist(api, max_dist):
     """Every traversal cap, odd and even (the texture walk takes two steps
