@@ -60,11 +60,13 @@ __device__ __forceinline__ bool block_ok(float u, float v, float uhi, float vhi)
     constexpr int R = (K - 1) / 2;
     const float fu = floorf(u), fv = floorf(v);
     bool ok = fu >= (float)(R + 1) && fu <= uhi && fv >= (float)(R + 1) && fv <= vhi;    // false for NaN
+    // Only the sums can round: for 2 <= u < 2^16 (maps are at most 65536
+    // texels wide) and d <= R, u - d is exact (a result at or above the
+    // binade of u keeps its spacing, one below it has a finer one), so
+    // floor(u - d) is floor(u) - d.
 #pragma unroll
-    for (int d = 1; d <= R; ++d) {
-        ok = ok && floorf(__fadd_rn(u, (float)d)) == fu + (float)d && floorf(__fadd_rn(u, (float)-d)) == fu - (float)d &&
-             floorf(__fadd_rn(v, (float)d)) == fv + (float)d && floorf(__fadd_rn(v, (float)-d)) == fv - (float)d;
-    }
+    for (int d = 1; d <= R; ++d)
+        ok = ok && floorf(__fadd_rn(u, (float)d)) == fu + (float)d && floorf(__fadd_rn(v, (float)d)) == fv + (float)d;
     return ok;
 }
 
