@@ -250,14 +250,16 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
             if (K <= 3) {
                 // all of the lane's edge samples, placed by a prefix sum
                 const uint32_t ne = (uint32_t)__popcll(edges);
-                uint32_t incl = ne;
+                uint32_t incl = ne, total = 0;
+                if (__any_sync(0xffffffffu, ne != 0)) {      // about one element in five has none
 #pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const uint32_t t2 = __shfl_up_sync(0xffffffffu, incl, off);
-                    if ((int)lane >= off)
-                        incl += t2;
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const uint32_t t2 = __shfl_up_sync(0xffffffffu, incl, off);
+                        if ((int)lane >= off)
+                            incl += t2;
+                    }
+                    total = __shfl_sync(0xffffffffu, incl, 31);
                 }
-                const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
                 if (total != 0u) {
                     int pos = queued + (int)(incl - ne);
                     uint64_t rest = edges;
