@@ -41,6 +41,27 @@ struct RpcfQueue {
     EdgeEntry q[kCap];
 };
 
+// A queued sample's number: for k = 3 its bit in the packed 5 x 5 block
+// word (row y at bits 5y..5y+4, sample (a, b) at block (a + 2, b + 2)), for
+// larger k its index (b + R) * K + (a + R) among the k x k samples.
+template <int K>
+__device__ __forceinline__ int sample_slot(int q)
+{
+    return K == 3 ? (q / 3 + 1) * 5 + q % 3 + 1 : q;
+}
+
+template <int K>
+__device__ __forceinline__ int sample_dx(int slot)
+{
+    return K == 3 ? slot % 5 - 2 : slot % K - (K - 1) / 2;
+}
+
+template <int K>
+__device__ __forceinline__ int sample_dy(int slot)
+{
+    return K == 3 ? slot / 5 - 2 : slot / K - (K - 1) / 2;
+}
+
 __device__ __forceinline__ uint32_t to_fix(float v)
 {
     return (uint32_t)__float2uint_rn(__fmul_rn(v, kFix));
@@ -159,8 +180,8 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
                 const EdgeEntry e = wq[warp].q[q];
                 const uint32_t i = e.idx;
                 const int sample = (int)e.bits_job;
-                const float ua = __fadd_rn(__fmul_rn(__ldg(x + i), W), (float)(sample % K - R));
-                const float vb = __fadd_rn(__fmul_rn(__ldg(y + i), H), (float)(sample / K - R));
+                const float ua = __fadd_rn(__fmul_rn(__ldg(x + i), W), (float)sample_dx<K>(sample));
+                const float vb = __fadd_rn(__fmul_rn(__ldg(y + i), H), (float)sample_dy<K>(sample));
                 const float pz = __ldg(z + i);
                 FragResult r;
                 uint32_t bits;
@@ -213,14 +234,26 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
                 // (a + 1, b + 1); it is an edge sample where one of Listing
                 // 2's four neighbours differs from it, else it adds its
                 // shadow test
-                constexpr uint32_t mk = (1u << K) - 1u;
+                if constexpr (K == 3) {
+                    // the whole 5 x 5 block in one word, row y at bits 5y..5y+4:
+                    // a sample differs from a neighbour one bit (left, right)
+                    // or five bits (below, above) away, so the four
+                    // comparisons of Listing 2 cover all nine samples at once
+                    const uint32_t P = rows[0] | (rows[1] << 5) | (rows[2] << 10) | (rows[3] << 15) | (rows[4] << 20);
+                    constexpr uint32_t kSamples = (7u << 6) | (7u << 11) | (7u << 16);   // rows 1-3, columns 1-3
+                    const uint32_t e = ((P ^ (P >> 1)) | (P ^ (P << 1)) | (P ^ (P >> 5)) | (P ^ (P << 5))) & kSamples;
+                    edges = e;
+                    base = (uint32_t)__popc(P & ~e & kSamples) << 25;
+                } else {
+                    constexpr uint32_t mk = (1u << K) - 1u;
 #pragma unroll
-                for (int b = 0; b < K; ++b) {
-                    const uint32_t c = (rows[b + 1] >> 1) & mk;
-                    const uint32_t e = (c ^ (rows[b + 1] & mk)) | (c ^ ((rows[b + 1] >> 2) & mk)) |
-                                       (c ^ ((rows[b + 2] >> 1) & mk)) | (c ^ ((rows[b] >> 1) & mk));
-                    edges |= (uint64_t)e << (K * b);
-                    base += (uint32_t)__popc(c & ~e) << 25;
+                    for (int b = 0; b < K; ++b) {
+                        const uint32_t c = (rows[b + 1] >> 1) & mk;
+                        const uint32_t e = (c ^ (rows[b + 1] & mk)) | (c ^ ((rows[b + 1] >> 2) & mk)) |
+                                           (c ^ ((rows[b + 2] >> 1) & mk)) | (c ^ ((rows[b] >> 1) & mk));
+                        edges |= (uint64_t)e << (K * b);
+                        base += (uint32_t)__popc(c & ~e) << 25;
+                    }
                 }
             } else {
 #pragma unroll
@@ -230,7 +263,7 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
                     const bool edge = valid && classify_uv<2, false>(m, __fadd_rn(u, (float)(q % K - R)),
                                                                      __fadd_rn(v, (float)(q / K - R)), ze, r, bits);
                     if (edge) {
-                        edges |= 1ull << q;
+                        edges |= 1ull << sample_slot<K>(q);
                     } else {
                         base += r.fil != 0.0f ? (1u << 25) : 0u;
                         single = r.fil;
