@@ -9,13 +9,15 @@
 // gathers or five loads each); off-edge samples add their shadow test at
 // once, edge samples go to the warp's queue (fragment and sample index; the
 // drain classifies the sample again) and are walked 32 at a time on full
-// warps.  For k > 1 the per-fragment sum is kept in the output plane as
-// a fixed-point integer with 25 fraction bits (each sample answer rounded to
-// 2^-25, at most 49 * 2^25 < 2^31 in total), so the adds of the deferred
-// samples commute and the result does not depend on their order; a second
-// pass turns the sum into the mean (bit 31 marks a NaN sample answer).
-// For k = 1 there is nothing to add and the answers are stored as floats
-// (rsmss_filter's bits).
+// warps.  For k > 1 a fragment with edge samples keeps its sum in the
+// output plane as a fixed-point integer (each sample answer rounded to
+// 2^-F, F = 24 / 22 / 20 for k = 3 / 5 / 7) below a count of its samples
+// still to come; the adds commute, so the result does not depend on their
+// order, and the add that takes the count to zero writes the mean in place.
+// A fragment without edge samples writes its mean at once, and one outside
+// the shared block (below) walks its own samples, so no second pass is
+// needed.  For k = 1 there is nothing to add and the answers are stored as
+// floats (rsmss_filter's bits).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -28,9 +30,20 @@ namespace rbsm {
 namespace {
 
 constexpr int kRpcfThreads = 256;
-constexpr float kFix = 33554432.0f;            // 2^25
-constexpr float kUnfix = 1.0f / 33554432.0f;   // 2^-25 (exact)
-constexpr uint32_t kNanFlag = 0x80000000u;     // above any sum (49 * 2^25 < 2^31): the mean is NaN
+
+// The fixed-point layout of a pending fragment: F fraction bits per sample
+// answer, the sum (at most K^2 * 2^F) below bit kCount, and the number of
+// samples still to be added at bits kCount..31 (at most K^2):
+// k = 3: 9 * 2^24 < 2^28, 9 < 2^4;  k = 5: 25 * 2^22 < 2^27, 25 < 2^5;
+// k = 7: 49 * 2^20 < 2^26, 49 < 2^6.  A sample answer is off by at most
+// 2^-(F+1), far inside the 1e-5 bar.
+template <int K>
+struct FixLayout {
+    static constexpr int kFrac = K == 3 ? 24 : K == 5 ? 22 : 20;
+    static constexpr int kCount = K == 3 ? 28 : K == 5 ? 27 : 26;
+    static_assert((unsigned long long)(K * K) << kFrac < (1ull << kCount), "sum overflows into the count");
+    static_assert(K * K < (1 << (32 - kCount)), "count overflows");
+};
 // Edge samples are queued per fragment element: for k <= 3 all of a lane's
 // edge samples at once (a warp prefix sum places them), so the queue holds
 // < 32 left over + k^2 samples of every lane; for larger k each lane's
@@ -62,9 +75,28 @@ __device__ __forceinline__ int sample_dy(int slot)
     return K == 3 ? slot / 5 - 2 : slot / K - (K - 1) / 2;
 }
 
+template <int K>
 __device__ __forceinline__ uint32_t to_fix(float v)
 {
-    return (uint32_t)__float2uint_rn(__fmul_rn(v, kFix));
+    return (uint32_t)__float2uint_rn(__fmul_rn(v, (float)(1u << FixLayout<K>::kFrac)));
+}
+
+// The mean of k^2 sample answers from their fixed-point sum.
+template <int K>
+__device__ __forceinline__ float mean_of(uint32_t sum)
+{
+    return __fdiv_rn(__fmul_rn(__uint2float_rn(sum), 1.0f / (float)(1u << FixLayout<K>::kFrac)), (float)(K * K));
+}
+
+// The same for a fragment without edge samples, whose answers are its c lit
+// samples: c / k^2.  For k = 3, c * RN(1/9) rounds to RN(c / 9) for every
+// c in 0..9 (checked for each c), so a multiply gives the division's bits.
+template <int K>
+__device__ __forceinline__ float mean_of_lit(uint32_t c)
+{
+    if (K == 3)
+        return __fmul_rn((float)c, 1.0f / 9.0f);
+    return __fdiv_rn((float)c, (float)(K * K));
 }
 
 // The shared block.  Sample (a, b)'s texel is clamp(floor(u + a)) with u + a
@@ -189,12 +221,17 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
                 // walks through the texture view (two steps per gather), except
                 // for k = 3, where the scalar walk measured 1 % faster
                 resolve_edge_uv<2, K == 3 ? 0 : 2>(m, ua, vb, pz, bits, max_dist, r);
-                if (K == 1)
+                if (K == 1) {
                     vis[i] = r.fil;
-                else if (r.fil != r.fil)
-                    atomicOr(acc + i, kNanFlag);      // a NaN answer (NaN or infinite coordinates)
-                else
-                    atomicAdd(acc + i, to_fix(r.fil));
+                } else {
+                    // queued samples come from fragments inside the shared
+                    // block (finite coordinates), whose answers are finite
+                    constexpr int C = FixLayout<K>::kCount;
+                    const uint32_t add = to_fix<K>(r.fil) - (1u << C);    // one sample fewer to come
+                    const uint32_t old = atomicAdd(acc + i, add);
+                    if ((old >> C) == 1u)                                  // the fragment's last sample
+                        vis[i] = mean_of<K>((old + add) & ((1u << C) - 1u));
+                }
             }
             __syncwarp();                  // entries read before they are overwritten
             queued = base;
@@ -227,7 +264,8 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
             uint64_t edges = 0;
             uint32_t base = 0;
             float single = 0.0f;
-            if (tex && valid && block_ok<K>(u, v, uhi, vhi)) {
+            const bool base_path = tex && valid && block_ok<K>(u, v, uhi, vhi);
+            if (base_path) {
                 uint32_t rows[K + 2];
                 block_bits<K>(m, u, v, ze, rows);
                 // a row of samples at once: sample (a, b)'s texel is block
@@ -243,7 +281,7 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
                     constexpr uint32_t kSamples = (7u << 6) | (7u << 11) | (7u << 16);   // rows 1-3, columns 1-3
                     const uint32_t e = ((P ^ (P >> 1)) | (P ^ (P << 1)) | (P ^ (P >> 5)) | (P ^ (P << 5))) & kSamples;
                     edges = e;
-                    base = (uint32_t)__popc(P & ~e & kSamples) << 25;
+                    base = (uint32_t)__popc(P & ~e & kSamples) << FixLayout<K>::kFrac;
                 } else {
                     constexpr uint32_t mk = (1u << K) - 1u;
 #pragma unroll
@@ -252,37 +290,51 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
                         const uint32_t e = (c ^ (rows[b + 1] & mk)) | (c ^ ((rows[b + 1] >> 2) & mk)) |
                                            (c ^ ((rows[b + 2] >> 1) & mk)) | (c ^ ((rows[b] >> 1) & mk));
                         edges |= (uint64_t)e << (K * b);
-                        base += (uint32_t)__popc(c & ~e) << 25;
+                        base += (uint32_t)__popc(c & ~e) << FixLayout<K>::kFrac;
                     }
                 }
-            } else {
-#pragma unroll
+            } else if (K == 1) {
+                FragResult r{0.0f, 0.0f, 0};
+                uint32_t bits = 0;
+                if (valid && classify_uv<2, false>(m, u, v, ze, r, bits))
+                    edges = 1ull << sample_slot<K>(0);
+                single = r.fil;
+            } else if (valid) {
+                // outside the shared block (the map's border rows and
+                // columns, or a non-finite coordinate): the lane walks its
+                // own edge samples and writes the mean (rare, so the
+                // divergence costs little)
+                uint32_t sum = 0;
+                bool nan = false;
+#pragma unroll 1
                 for (int q = 0; q < K * K; ++q) {
                     FragResult r{0.0f, 0.0f, 0};
                     uint32_t bits = 0;
-                    const bool edge = valid && classify_uv<2, false>(m, __fadd_rn(u, (float)(q % K - R)),
-                                                                     __fadd_rn(v, (float)(q / K - R)), ze, r, bits);
-                    if (edge) {
-                        edges |= 1ull << sample_slot<K>(q);
-                    } else {
-                        base += r.fil != 0.0f ? (1u << 25) : 0u;
-                        single = r.fil;
-                    }
+                    const float ua = __fadd_rn(u, (float)(q % K - R)), vb = __fadd_rn(v, (float)(q / K - R));
+                    if (classify_uv<2, false>(m, ua, vb, ze, r, bits))
+                        resolve_edge_uv<2, K == 3 ? 0 : 2>(m, ua, vb, ze, bits, max_dist, r);
+                    if (r.fil != r.fil)
+                        nan = true;               // a NaN answer (NaN or infinite coordinates)
+                    else
+                        sum += to_fix<K>(r.fil);
                 }
+                vis[t.first + s] = nan ? __int_as_float(0x7fc00000) : mean_of<K>(sum);
             }
             // the base value is stored before any deferred sample of this
             // fragment can add to it ...
+            const uint32_t ne = (uint32_t)__popcll(edges);
             if (valid) {
                 if (K == 1)
                     vis[t.first + s] = single;
-                else
-                    acc[t.first + s] = base;
+                else if (ne != 0)
+                    acc[t.first + s] = (ne << FixLayout<K>::kCount) | base;
+                else if (base_path)
+                    vis[t.first + s] = mean_of_lit<K>(base >> FixLayout<K>::kFrac);
             }
             // ... then the edge samples are queued and walked whenever 32
             // are waiting
             if (K <= 3) {
                 // all of the lane's edge samples, placed by a prefix sum
-                const uint32_t ne = (uint32_t)__popcll(edges);
                 uint32_t incl = ne, total = 0;
                 if (__any_sync(0xffffffffu, ne != 0)) {      // about one element in five has none
 #pragma unroll
@@ -329,21 +381,6 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
     drain(queued, true);
 }
 
-// The mean from the fixed-point sum: (sum * 2^-25) / k^2, or NaN when a
-// sample's answer was NaN (as a float sum would carry it).
-template <int K>
-__global__ void __launch_bounds__(256) rpcf_finish(float *__restrict__ vis, long long n)
-{
-    uint32_t *acc = reinterpret_cast<uint32_t *>(vis);
-    const float count = (float)(K * K);
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint32_t a = acc[i];
-        vis[i] = (a & kNanFlag) ? __int_as_float(0x7fc00000)
-                                : __fdiv_rn(__fmul_rn(__uint2float_rn(a), kUnfix), count);
-    }
-}
-
 template <int K>
 int launch_rpcf(const rbsm_map &map, const rbsm_frags &f, float *vis, int max_dist, cudaStream_t stream)
 {
@@ -366,14 +403,6 @@ int launch_rpcf(const rbsm_map &map, const rbsm_frags &f, float *vis, int max_di
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return cuda_fail(e);
-    if (K > 1) {
-        long long blocks = (f.n + 255) / 256;
-        if (blocks > 8LL * sms)
-            blocks = 8LL * sms;
-        rpcf_finish<K><<<(unsigned)blocks, 256, 0, stream>>>(vis, f.n);
-        if ((e = cudaGetLastError()) != cudaSuccess)
-            return cuda_fail(e);
-    }
     return RBSM_OK;
 }
 

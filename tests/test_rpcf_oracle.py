@@ -94,3 +94,14 @@ def test_bad_k_is_rejected():
     for k in (0, 2, 9, -1):
         with pytest.raises(ValueError):
             orc.rpcf(d, x, x, x, k=k)
+
+
+def test_thirds_of_nine_by_multiplication():
+    """The RPCF kernel takes the mean of a k = 3 fragment without edge
+    samples as c * RN(1/9) for its c lit samples; that is RN(c / 9), the
+    division's result, for every c in 0..9 (float32), and not for 25 or 49
+    samples, which keep the division."""
+    inv = np.float32(1.0) / np.float32(9.0)
+    for c in range(10):
+        assert np.float32(c) * inv == np.float32(c) / np.float32(9.0), c
+    assert any(np.float32(c) * (np.float32(1) / np.float32(25)) != np.float32(c) / np.float32(25) for c in range(26))
