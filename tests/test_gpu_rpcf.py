@@ -92,15 +92,19 @@ def test_empty(api):
     assert v.shape == (0,)
 
 
+@pytest.mark.parametrize("k", [3, 5, 7])
 @pytest.mark.parametrize("w,h", [(1, 1), (2, 2), (1, 9), (9, 1), (3, 700), (257, 129)])
-def test_odd_maps_and_borders(api, w, h):
+def test_odd_maps_and_borders(api, w, h, k):
+    """Clamped borders and NaN / infinite coordinates: fragments outside the
+    shared block, whose samples the lane walks itself, beside block
+    fragments whose sums count their pending samples."""
     rng = np.random.default_rng(w * 1000 + h)
     depth = np.where(rng.random((h, w)) < 0.35, np.float32(0.25), np.float32(1.0)).astype(np.float32)
     x = rng.uniform(-0.3, 1.3, 6000).astype(np.float32)
     y = rng.uniform(-0.3, 1.3, 6000).astype(np.float32)
     x[::71] = np.nan
     y[::67] = np.inf
-    check(api, depth, x, y, np.full_like(x, 0.5), 3, "%dx%d" % (w, h))
+    check(api, depth, x, y, np.full_like(x, 0.5), k, "%dx%d k %d" % (w, h, k))
 
 
 @pytest.mark.parametrize("max_dist", [1, 2, 16, 255])
