@@ -285,7 +285,7 @@ int rbsm_batch_run(const rbsm_batch *batch, void *workspace, size_t workspace_by
 /*
  * rbsm_batch_run without a workspace argument, for callers that cannot
  * allocate device memory: a plugin running inside a host application that
- * owns every device allocation, or a frame loop with a fixed memory budget
+ * owns every device allocation, or a frame loop with a fixed memory footprint
  * that must not allocate while frames are in flight.  The paper has no
  * counterpart; this is a convenience of the library.
  *

@@ -280,7 +280,7 @@ def test_surrogate_meets_its_stated_bound_on_held_out_scenes(lib, recipe):
     vis = job.vis_filter.cpu().numpy().astype(np.float64)
     answered = ((codes >> 10) & 1) == 1
     assert answered.sum() == acc > 10000
-    # judge: the oracle's Listing 5 answer of every answered fragment
+    # reference answers: the oracle's Listing 5 answer of every answered fragment
     ref = orc.evaluate(f.depth, f.x[answered], f.y[answered], f.z[answered], orc.MODE_FILTER)
     assert np.all(((ref["codes"] >> 9) & 1) == 1)                  # only edge fragments are answered
     feat = orc.features(f.depth, f.x[answered], f.y[answered], f.z[answered])

@@ -253,6 +253,48 @@ def _texture(api, depth):
     return api.MapTexture(depth)
 
 
+@pytest.mark.parametrize("w,h", [(65536, 3), (3, 65536)])
+def test_maximum_extent(api, w, h):
+    """Maps at the largest extent a side may have (65536 texels): positions
+    just below every power of two up to 2^16 and at the far border along the
+    long side, both modes against the oracle, with plain loads and, where
+    the device's texture limits take the map, texture gathers.  Only the
+    tall map may be refused a texture (pitch-linear textures are limited in
+    height)."""
+    from paper_1711_07793_gb300 import _native as N
+    rng = np.random.default_rng(w + 7 * h)
+    depth, x, y, z = _random_case(rng, w, h, 30000, spread=0.05)
+    long_side = max(w, h)
+    pos = []
+    for p in range(1, 17):
+        b = 2.0 ** p
+        for t in range(4):
+            pos += [b - t * b * 2.0 ** -24, b - 1.0 - t * b * 2.0 ** -24, b + 0.5]
+    pos += [long_side - 0.25, long_side - 1.0, long_side - 1.5]
+    pos = np.array(pos, np.float64)
+    pos = np.unique(pos[(pos >= 0) & (pos < long_side)].astype(np.float32))
+    t_long = (np.repeat(pos.astype(np.float64), 40) / long_side).astype(np.float32)
+    t_short = rng.uniform(0, 1, t_long.size).astype(np.float32)
+    z_more = np.array([0.25, 0.5, 0.75, 1.0], np.float32)[rng.integers(0, 4, t_long.size)]
+    if w > h:
+        x, y = np.concatenate([x, t_long]), np.concatenate([y, t_short])
+    else:
+        x, y = np.concatenate([x, t_short]), np.concatenate([y, t_long])
+    z = np.concatenate([z, z_more])
+    check_both(api, depth, x, y, z, "%dx%d" % (w, h))
+    d = dev(depth)
+    try:
+        tex = _texture(api, d)
+    except N.RBSMError as e:
+        assert e.code == N.RBSM_ERR_ARG and h > w
+        return
+    for mode in (orc.MODE_SILHOUETTE, orc.MODE_FILTER):
+        ref = orc.evaluate(depth, x, y, z, mode)
+        vis, cod = run_gpu(api, tex, x, y, z, mode)
+        assert_parity(vis, cod, ref, mode, "%dx%d texture mode %d" % (w, h, mode))
+    tex.close()
+
+
 def test_texture_refused_only_for_unaligned_rows(api):
     """rbsm_map_texture_create answers RBSM_ERR_ARG for rows that break the
     device's pitch alignment, and nothing else."""

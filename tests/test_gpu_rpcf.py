@@ -167,3 +167,31 @@ def test_shared_block_conditions(api, k):
     y = (vv / h).astype(np.float32)
     z = np.full_like(x, 0.5)
     check(api, depth, x, y, z, k, "block k=%d" % k)
+
+
+@pytest.mark.parametrize("k", [3, 5, 7])
+def test_shared_block_at_the_maximum_extent(api, k):
+    """The shared-block test at the largest map width (65536 texels): for
+    positions just below 2^14, 2^15 and 2^16 minus a whole offset, u + a can
+    round up while u - a stays exact (the kernel relies on the latter for
+    every u below 2^16), and the far border clamps; answers equal the
+    oracle's, texture gathers equal plain loads."""
+    w, h = 65536, 12
+    rng = np.random.default_rng(100 + k)
+    depth = np.where(rng.random((h, w)) < 0.35, np.float32(0.25), np.float32(1.0)).astype(np.float32)
+    us = []
+    for b in (16384.0, 32768.0, 65536.0):
+        ulp = b * 2.0 ** -24                      # spacing of the floats just below b
+        for a in range(0, 4):
+            for t in range(0, 6):
+                us.append(b - a - t * ulp)
+                us.append(b - a - t * 2.0 * ulp)
+    us += [65529.5, 65530.0, 65532.25, 65533.0, 65534.75, 65535.0, 65535.5, 65535.99609375]
+    u = np.unique(np.array(us, np.float32).astype(np.float64))
+    u = u[(u >= 0) & (u < w)]
+    uu = np.repeat(u, 6)
+    x = (uu / w).astype(np.float32)
+    assert np.array_equal(x.astype(np.float64) * w, uu)   # u = x * 65536 exactly
+    y = (rng.uniform(0, h, uu.size) / h).astype(np.float32)
+    z = np.full_like(x, 0.5)
+    check(api, depth, x, y, z, k, "max extent k=%d" % k)
