@@ -7,9 +7,9 @@
 // Same warp-tile scheme as the other kernels, with the sample as the unit
 // of deferred work: a lane classifies its fragments' samples (two texture
 // gathers or five loads each); off-edge samples add their shadow test at
-// once, edge samples go to the warp's queue (fragment and sample index; the
-// drain classifies the sample again) and are walked 32 at a time on full
-// warps.  For k > 1 a fragment with edge samples keeps its sum in the
+// once, edge samples go to the warp's queue (fragment and sample index; for
+// k = 3 with the fragment's shadow tests, else the drain classifies the
+// sample again) and are walked 32 at a time on full warps.  For k > 1 a fragment with edge samples keeps its sum in the
 // output plane as a fixed-point integer (each sample answer rounded to
 // 2^-F, F = 24 / 22 / 20 for k = 3 / 5 / 7) below a count of its samples
 // still to come; the adds commute, so the result does not depend on their
@@ -56,7 +56,8 @@ struct RpcfQueue {
 
 // A queued sample's number: for k = 3 its bit in the packed 5 x 5 block
 // word (row y at bits 5y..5y+4, sample (a, b) at block (a + 2, b + 2)), for
-// larger k its index (b + R) * K + (a + R) among the k x k samples.
+// larger k its index (b + R) * K + (a + R) among the k x k samples.  A k = 3
+// entry holds the number in bits 0-4 and the fragment's block word above it.
 template <int K>
 __device__ __forceinline__ int sample_slot(int q)
 {
@@ -211,13 +212,24 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
             if (q < queued) {
                 const EdgeEntry e = wq[warp].q[q];
                 const uint32_t i = e.idx;
-                const int sample = (int)e.bits_job;
+                const int sample = K == 3 ? (int)(e.bits_job & 31u) : (int)e.bits_job;
                 const float ua = __fadd_rn(__fmul_rn(__ldg(x + i), W), (float)sample_dx<K>(sample));
                 const float vb = __fadd_rn(__fmul_rn(__ldg(y + i), H), (float)sample_dy<K>(sample));
                 const float pz = __ldg(z + i);
-                FragResult r;
+                FragResult r{0.0f, 0.0f, 0};
                 uint32_t bits;
-                classify_uv<2, false>(m, ua, vb, pz, r, bits);    // the sample's discontinuity again
+                if (K == 3) {
+                    // the entry carries the fragment's block word: the
+                    // sample's shadow test and its four neighbours' (left,
+                    // right one bit away, +y, -y five bits away) are bits of
+                    // it, taken with the same depth from the same texels
+                    const uint32_t P = e.bits_job >> 5;
+                    const uint32_t s0 = (P >> sample) & 1u;
+                    bits = s0 | ((((P >> (sample - 1)) & 1u) ^ s0) << 1) | ((((P >> (sample + 1)) & 1u) ^ s0) << 2) |
+                           ((((P >> (sample + 5)) & 1u) ^ s0) << 3) | ((((P >> (sample - 5)) & 1u) ^ s0) << 4);
+                } else {
+                    classify_uv<2, false>(m, ua, vb, pz, r, bits);    // the sample's discontinuity again
+                }
                 // walks through the texture view (two steps per gather), except
                 // for k = 3, where the scalar walk measured 1 % faster
                 resolve_edge_uv<2, K == 3 ? 0 : 2>(m, ua, vb, pz, bits, max_dist, r);
@@ -262,7 +274,7 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
             // all samples' texel reads first; off-edge samples add their
             // shadow test to the base value, edge samples set their bit
             uint64_t edges = 0;
-            uint32_t base = 0;
+            uint32_t base = 0, block = 0;
             float single = 0.0f;
             const bool base_path = tex && valid && block_ok<K>(u, v, uhi, vhi);
             if (base_path) {
@@ -281,6 +293,7 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
                     constexpr uint32_t kSamples = (7u << 6) | (7u << 11) | (7u << 16);   // rows 1-3, columns 1-3
                     const uint32_t e = ((P ^ (P >> 1)) | (P ^ (P << 1)) | (P ^ (P >> 5)) | (P ^ (P << 5))) & kSamples;
                     edges = e;
+                    block = P;
                     base = (uint32_t)__popc(P & ~e & kSamples) << FixLayout<K>::kFrac;
                 } else {
                     constexpr uint32_t mk = (1u << K) - 1u;
@@ -351,7 +364,7 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
                     while (rest) {
                         const int q = __ffsll((long long)rest) - 1;
                         rest &= rest - 1;
-                        wq[warp].q[pos++] = EdgeEntry{(uint32_t)(t.first + s), (uint32_t)q};
+                        wq[warp].q[pos++] = EdgeEntry{(uint32_t)(t.first + s), K == 3 ? (block << 5) | (uint32_t)q : (uint32_t)q};
                     }
                     queued += (int)total;
                     drain(queued, false);
