@@ -590,6 +590,26 @@ int rbsm_mlp_reset_loss(void *state, void *stream);
 /* Network outputs (n x 2 floats: estimate, error estimate) of n samples. */
 int rbsm_mlp_forward(const void *state, const rbsm_sample *samples, int64_t n, float *out, void *stream);
 
+/*
+ * Diagnostic of the bounded waits.  Every tensor-core kernel of the library
+ * waits for its products on mbarriers through one routine that gives up
+ * after a time limit of the device's global timer; the kernel then records
+ * RBSM_ERR_TIMEOUT and returns instead of hanging.  This call runs that routine in one thread of one CTA
+ * on a barrier that nothing arrives at, with limit_ns (1e3 ... 1e9
+ * nanoseconds), and then on the same barrier after one arrival.
+ *
+ *   out: device pointer to 3 uint64_t (8-byte aligned), written
+ *     out[0] = 1 when the first wait gave up (expected), else 0;
+ *     out[1] = 1 when the second wait completed (expected), else 0;
+ *     out[2] = nanoseconds the first wait took (the device's global timer).
+ *
+ * Asynchronous on `stream`.  Returns RBSM_ERR_ARG for a null or unaligned
+ * `out` or a limit outside the range, RBSM_ERR_CUDA when the launch fails.
+ * Not part of the method; it lets a caller check the timeout path on its
+ * own hardware without faulting or hanging the GPU.
+ */
+int rbsm_selftest_bounded_wait(uint64_t limit_ns, uint64_t *out, void *stream);
+
 /* Text for a return code. */
 const char *rbsm_status_string(int code);
 

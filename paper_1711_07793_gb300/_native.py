@@ -187,6 +187,8 @@ def _declare(lib):
     lib.rbsm_mlp_reset_loss.argtypes = [vp, vp]
     lib.rbsm_mlp_forward.restype = i32
     lib.rbsm_mlp_forward.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
+    lib.rbsm_selftest_bounded_wait.restype = i32
+    lib.rbsm_selftest_bounded_wait.argtypes = [ctypes.c_uint64, vp, vp]
     lib.rbsm_status_string.restype = ctypes.c_char_p
     lib.rbsm_status_string.argtypes = [i32]
     lib.rbsm_last_cuda_error.restype = i32

@@ -509,3 +509,15 @@ def rbsm_visibility_gbuffer(jobs, mode=N.RBSM_MODE_BOTH, max_dist=N.RBSM_MAXDIST
     N.check("rbsm_visibility_gbuffer",
             N.lib().rbsm_visibility_gbuffer(arr, len(jobs), int(mode), ctypes.byref(p), _stream_handle(stream)))
     return jobs
+
+
+def rbsm_selftest_bounded_wait(limit_ns=2_000_000, stream=None):
+    """Runs the library's bounded mbarrier wait on a barrier nothing arrives
+    at, then after one arrival (rbsm_selftest_bounded_wait); returns
+    (gave_up, completed_after_arrival, waited_ns) once the stream is done."""
+    out = torch.zeros(3, dtype=torch.int64, device="cuda")
+    N.check("rbsm_selftest_bounded_wait",
+            N.lib().rbsm_selftest_bounded_wait(int(limit_ns), ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+    (stream if stream is not None else torch.cuda.current_stream()).synchronize()
+    o = out.cpu().tolist()
+    return bool(o[0]), bool(o[1]), int(o[2])

@@ -78,7 +78,8 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 }
 
 // Wait for the phase with the given parity to complete; gives up (false)
-// after limit_ns nanoseconds of the global timer.
+// after limit_ns nanoseconds of the global timer (rbsm_selftest_bounded_wait
+// runs this routine on a barrier nothing arrives at).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns)
 {
     const uint32_t a = smem_addr(bar);
@@ -95,6 +96,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64
         if (global_ns() - t0 > limit_ns)
             return false;
     }
+}
+
+// One arrival on the barrier (this thread's).
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_addr(bar)) : "memory");
 }
 
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }

@@ -123,6 +123,12 @@ def test_bad_arguments_are_rejected_before_any_cuda_call(native):
     assert lib.rbsm_mlp_set_trust(None, None, None) == N.RBSM_ERR_ARG
     assert lib.rbsm_mlp_set_trust(state + 8, None, None) == N.RBSM_ERR_ARG
     assert lib.rbsm_batch_noalloc_counts(None, None) == N.RBSM_ERR_ARG
+    words = (ctypes.c_uint64 * 4)()
+    wa = ctypes.addressof(words)
+    assert lib.rbsm_selftest_bounded_wait(1_000_000, None, None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_selftest_bounded_wait(1_000_000, wa + 4, None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_selftest_bounded_wait(999, wa, None) == N.RBSM_ERR_ARG
+    assert lib.rbsm_selftest_bounded_wait(1_000_000_001, wa, None) == N.RBSM_ERR_ARG
     bad_flags = N.rbsm_params(16, 2)
     counter = (ctypes.c_uint64 * 1)()
     assert lib.rbsm_mlp_dataset(B(good_map), B(good_frags), B(bad_flags), addr, 4, counter, None) == N.RBSM_ERR_ARG

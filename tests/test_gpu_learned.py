@@ -290,3 +290,17 @@ def test_surrogate_meets_its_stated_bound_on_held_out_scenes(lib, recipe):
     err = np.abs(vis[answered] - ref["vis"])
     got = {"mean": err.mean(), "p99": np.quantile(err, 0.99), "max": err.max()}
     assert all(got[k] <= BOUND[k] for k in BOUND), (got, acc, fb)
+
+
+@pytest.mark.parametrize("limit_ns", [20_000, 2_000_000])
+def test_bounded_wait_gives_up_instead_of_hanging(lib, limit_ns):
+    """The mbarrier wait every tensor-core kernel uses gives up after its
+    limit on a barrier that nothing arrives at (so a lost completion becomes
+    RBSM_ERR_TIMEOUT, not a hung GPU), completes once the barrier has its
+    arrival, and the context stays usable afterwards."""
+    api, _ = lib
+    gave_up, completed, waited = api.rbsm_selftest_bounded_wait(limit_ns)
+    assert gave_up and completed
+    assert limit_ns <= waited < limit_ns + 100_000_000
+    t = torch.arange(8, device="cuda", dtype=torch.float32)
+    assert float(t.sum()) == 28.0
