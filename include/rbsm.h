@@ -201,7 +201,13 @@ int rbsm_visibility_gbuffer(const rbsm_gbuffer_job *jobs, int32_t n_jobs, int32_
  * position (x W, y H), shifted by whole texels (u + a, v + b) for a, b in
  * -(k-1)/2 .. (k-1)/2 (float32 adds), each with the fragment's depth,
  * summed with b outer and a inner.  k = 1 is rsmss_filter itself.
- *   k: odd, 1..RBSM_RPCF_MAX_K.  vis: output, n floats in [0, 1].
+ *   k: odd, 1..RBSM_RPCF_MAX_K.  vis: output, n floats in [0, 1]; while
+ *   the call runs it also holds the pending fragments' partial sums, so it
+ *   must not overlap the fragment planes or the map.
+ * For k > 1 the sample answers are added in fixed point, each rounded to
+ * 2^-24, 2^-22 or 2^-20 (k = 3, 5, 7), so a result does not depend on the
+ * order in which a fragment's samples are finished and lies within
+ * k^2 * 2^-(F+1) of the exact mean of the sample answers.
  * Errors as for rsmss_filter, and RBSM_ERR_ARG for an even or out-of-range k.
  */
 #define RBSM_RPCF_MAX_K 7
