@@ -138,6 +138,12 @@ def test_bad_arguments_are_rejected_before_any_cuda_call(native):
     assert lib.rbsm_rpcf(B(good_map), B(good_frags), None, 3, B(p), None) == N.RBSM_ERR_ARG
     assert lib.rbsm_rpcf(B(good_map), B(good_frags), addr + 2, 3, B(p), None) == N.RBSM_ERR_ARG
     assert lib.rbsm_rpcf(B(good_map), B(N.rbsm_frags(None, None, None, 0)), None, 3, None, None) == N.RBSM_OK
+    # the output holds partial sums while the kernel runs: overlapping an input is refused
+    planes = (ctypes.c_float * 64)()
+    pa = ctypes.addressof(planes)
+    sep_frags = N.rbsm_frags(pa, pa + 64, pa + 128, 16)
+    for vis_at in (pa, pa + 96, pa + 188, addr + 60):       # over x, y, z, the map
+        assert lib.rbsm_rpcf(B(good_map), B(sep_frags), vis_at, 3, B(p), None) == N.RBSM_ERR_ARG
     maps = (N.rbsm_map * 1)(good_map)
     jobs = (N.rbsm_job * 1)(N.rbsm_job(0, 3, good_frags, addr, addr, None))
     batch = N.rbsm_batch(maps, 1, jobs, 1, p, 0, 0)
