@@ -24,6 +24,10 @@
  *   - Fragments: three float32 planes x[n], y[n], z[n] (structure of arrays).
  *     Any 4-byte alignment is accepted; 16-byte aligned planes and outputs
  *     take the vectorised path.
+ *   - Outputs must not overlap the inputs: an edge fragment's coordinates
+ *     are read again after the answers of its tile have been stored.  The
+ *     single-map calls and rbsm_rpcf refuse an output that overlaps their
+ *     fragment planes or map (RBSM_ERR_ARG).
  *   - Codes (optional uint16 per fragment):
  *       bits 0-3  discontinuity directions of Eq. 3: left, right, +y, -y
  *                 (+y = next row index)

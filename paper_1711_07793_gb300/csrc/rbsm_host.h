@@ -14,6 +14,8 @@ int cuda_fail(cudaError_t e);
 int check_map(const rbsm_map *m);
 int check_frags(const rbsm_frags *f);
 int check_params(const rbsm_params *p, int *max_dist);
+// True when [out, out + bytes) overlaps the fragment planes or the map.
+bool overlaps_inputs(const rbsm_map &m, const rbsm_frags &f, const void *out, size_t bytes);
 bool aligned16(const void *p);
 int device_sm_count();
 MapDev to_dev(const rbsm_map &m);

@@ -171,6 +171,18 @@ int launch_plain(const rbsm_map &map, const rbsm_frags &f, float *sil, float *fi
     return RBSM_OK;
 }
 
+bool overlaps_inputs(const rbsm_map &m, const rbsm_frags &f, const void *out, size_t bytes)
+{
+    const uintptr_t o0 = reinterpret_cast<uintptr_t>(out), o1 = o0 + bytes;
+    auto hit = [&](const void *p, uintptr_t n) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+        return a < o1 && o0 < a + n;
+    };
+    const uintptr_t plane = (uintptr_t)f.n * 4u;
+    const uintptr_t map_bytes = ((uintptr_t)(m.height - 1) * (uintptr_t)m.pitch + (uintptr_t)m.width) * 4u;
+    return hit(f.x, plane) || hit(f.y, plane) || hit(f.z, plane) || hit(m.depth, map_bytes);
+}
+
 int plain_entry(int mode, const rbsm_map *map, const rbsm_frags *frags, float *vis, uint16_t *codes,
                 const rbsm_params *params, void *stream)
 {
@@ -184,6 +196,9 @@ int plain_entry(int mode, const rbsm_map *map, const rbsm_frags *frags, float *v
         return RBSM_ERR_ARG;
     if (frags->n == 0)
         return RBSM_OK;
+    if (overlaps_inputs(*map, *frags, vis, (size_t)frags->n * 4u) ||
+        (codes && overlaps_inputs(*map, *frags, codes, (size_t)frags->n * 2u)))
+        return RBSM_ERR_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (mode == RBSM_MODE_SILHOUETTE)
         return codes ? launch_plain<1, true>(*map, *frags, vis, nullptr, codes, max_dist, s)

@@ -439,15 +439,7 @@ extern "C" int rbsm_rpcf(const rbsm_map *map, const rbsm_frags *frags, float *vi
     if (frags->n == 0)
         return RBSM_OK;
     // vis holds partial sums while the kernel runs: it must not overlap an input
-    const uintptr_t v0 = reinterpret_cast<uintptr_t>(vis), v1 = v0 + (uintptr_t)frags->n * 4u;
-    auto overlaps = [&](const void *p, uintptr_t bytes) {
-        const uintptr_t a = reinterpret_cast<uintptr_t>(p);
-        return a < v1 && v0 < a + bytes;
-    };
-    const uintptr_t plane = (uintptr_t)frags->n * 4u;
-    const uintptr_t map_bytes = ((uintptr_t)(map->height - 1) * (uintptr_t)map->pitch + (uintptr_t)map->width) * 4u;
-    if (overlaps(frags->x, plane) || overlaps(frags->y, plane) || overlaps(frags->z, plane) ||
-        overlaps(map->depth, map_bytes))
+    if (overlaps_inputs(*map, *frags, vis, (size_t)frags->n * 4u))
         return RBSM_ERR_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     switch (k) {

@@ -144,6 +144,11 @@ def test_bad_arguments_are_rejected_before_any_cuda_call(native):
     sep_frags = N.rbsm_frags(pa, pa + 64, pa + 128, 16)
     for vis_at in (pa, pa + 96, pa + 188, addr + 60):       # over x, y, z, the map
         assert lib.rbsm_rpcf(B(good_map), B(sep_frags), vis_at, 3, B(p), None) == N.RBSM_ERR_ARG
+        for fn in (lib.rbsm_visibility, lib.rsmss_filter):
+            assert fn(B(good_map), B(sep_frags), vis_at, None, B(p), None) == N.RBSM_ERR_ARG
+    codes_buf = (ctypes.c_uint16 * 64)()
+    for fn in (lib.rbsm_visibility, lib.rsmss_filter):             # codes over z
+        assert fn(B(good_map), B(sep_frags), ctypes.addressof(codes_buf), pa + 150, B(p), None) == N.RBSM_ERR_ARG
     maps = (N.rbsm_map * 1)(good_map)
     jobs = (N.rbsm_job * 1)(N.rbsm_job(0, 3, good_frags, addr, addr, None))
     batch = N.rbsm_batch(maps, 1, jobs, 1, p, 0, 0)
