@@ -649,10 +649,19 @@ def measure_rpcf(api, maps, xyz, frames, n_frag, args, stream, k=3):
     ms = timed(rpcf)
     ms_rsmss = timed(rsmss)
     fps = lambda t: frames * n_frag / (t * 1e-3) / 1e9
+    # the other filter sizes on the first 8 frames (one launch per frame)
+    few = min(frames, 8)
+    by_k = {}
+    for kk in (1, 5, 7):
+        def rpcf_k(kk=kk):
+            for f in range(few):
+                api.rbsm_rpcf(maps[f], xyz[f][0], xyz[f][1], xyz[f][2], k=kk, vis=outs[f])
+        by_k[str(kk)] = few * n_frag / (timed(rpcf_k) * 1e-3) / 1e9
     return {"metric": "Gfragments/s RPCF visibility (k x k PCF over RSMSS), same frames, one launch per frame",
             "k": k, "value": fps(ms), "ms_per_step": ms, "launches_per_step": frames,
             "rsmss_same_launches": {"value": fps(ms_rsmss), "ms_per_step": ms_rsmss},
-            "samples_per_fragment": k * k}
+            "samples_per_fragment": k * k,
+            "other_k_gfrag_s": {"frames": few, **by_k}}
 
 
 def measure_light_pass(api, c5, maps, frames, n_frag, step_fn, stream):
