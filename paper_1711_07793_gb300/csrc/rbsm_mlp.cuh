@@ -54,11 +54,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return *reinterpret_cast<uint32_t *>(&v);
 }
 
-__device__ __forceinline__ float bf16_to_float(uint16_t h)
-{
-    return __uint_as_float((uint32_t)h << 16);
-}
-
 __device__ __forceinline__ uint16_t float_to_bf16(float f)
 {
     __nv_bfloat16 v = __float2bfloat16_rn(f);
