@@ -86,3 +86,28 @@ def test_edge_statistics_invariants():
     assert 0 < n_edge < 4000
     assert e["walks"] == 4 * n_edge == sum(h["end_found"]) + sum(h["no_end"])
     assert h["end_found"][-1] == 0 and e["capped_walks"] == h["no_end"][-1]
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    """--impl reference: rank 0 times the oracle on the host cores and prints
+    one JSON line with the arm's keys; other ranks print nothing."""
+    import json
+    import rbsm_scenes as sc
+
+    class Tiny:
+        def __init__(self, seed):
+            self.f = sc.config1(seed)
+
+        def frame(self, k):
+            return self.f
+
+    monkeypatch.setattr(sc, "Config5", Tiny)
+    args = bench.parse_args(["--impl", "reference", "--steps", "2", "--warmup", "1"])
+    bench.run_reference(args, 1, 2)
+    assert capsys.readouterr().out == ""
+    bench.run_reference(args, 0, 1)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 1
+    assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert line["metric"] == bench.METRIC and line["higher_is_better"] is True
