@@ -216,9 +216,11 @@ constexpr size_t batch_smem_bytes()
 }
 
 // Persistent warps claim chunks of chunk_tiles warp tiles from the work
-// counter.  The claim of the next chunk is issued when the current one
-// starts, and its value is read only when the warp gets there, so the
-// atomic's latency hides behind a chunk of work.  While a warp works on one
+// counter, except that the last tiles of the launch (two per warp) go out
+// one per claim, so that warps finish together instead of some running a
+// whole chunk past the others.  The claim of the next chunk is issued when
+// the current one starts, and its value is read only when the warp gets
+// there, so the atomic's latency hides behind a chunk of work.  While a warp works on one
 // tile, the asynchronous copies of its next tile's coordinates into the
 // warp's shared-memory buffer are in flight: the tile is read out of the
 // buffer into registers, the buffer is refilled with the next tile, and the
@@ -264,7 +266,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const __gri
     if (lane == 0)
         claim = atomicAdd(a.counter, 1ull);
     const int chunk = a.chunk_tiles;
-    long long tile = (long long)__shfl_sync(0xffffffffu, claim, 0) * chunk;
+    // claims below c1 take `chunk` tiles, later ones a single tile, so the
+    // last tiles (about two per warp) are spread one at a time
+    const long long tail = 2ll * gridDim.x * (kThreads / 32);
+    const long long c1 = total > tail ? (total - tail) / chunk : 0;
+    long long c0 = (long long)__shfl_sync(0xffffffffu, claim, 0);
+    long long tile = c0 < c1 ? c0 * chunk : c1 * chunk + (c0 - c1);
+    int csz = c0 < c1 ? chunk : 1;
     if (tile >= total)
         return;
     if (lane == 0)
@@ -289,11 +297,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) batch_kernel(const __gri
     int fb_queued = 0;                         // learned variant: guard-tripped fragments waiting to walk
     for (;;) {
         long long nt;
-        if (in_chunk + 1 < chunk) {
+        if (in_chunk + 1 < csz) {
             nt = tile + 1;
             in_chunk += 1;
         } else {
-            nt = (long long)__shfl_sync(0xffffffffu, claim, 0) * chunk;
+            const long long c = (long long)__shfl_sync(0xffffffffu, claim, 0);
+            nt = c < c1 ? c * chunk : c1 * chunk + (c - c1);
+            csz = c < c1 ? chunk : 1;
             in_chunk = 0;
             if (nt < total && lane == 0)
                 claim = atomicAdd(a.counter, 1ull);
