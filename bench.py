@@ -624,6 +624,7 @@ def measure_rpcf(api, maps, xyz, frames, n_frag, args, stream, k=3):
     as RSMSS: the k x k samples re-read texels that are already on chip)."""
     import torch
     outs = [torch.empty(n_frag, dtype=torch.float32, device=xyz[0].device) for _ in range(frames)]
+    ws = torch.zeros(2, dtype=torch.int64, device=xyz[0].device)     # the tile counter of rbsm_rpcf_ws
     steps = max(3, min(args.steps // 20, 20))
 
     def timed(fn):
@@ -640,7 +641,7 @@ def measure_rpcf(api, maps, xyz, frames, n_frag, args, stream, k=3):
 
     def rpcf():
         for f in range(frames):
-            api.rbsm_rpcf(maps[f], xyz[f][0], xyz[f][1], xyz[f][2], k=k, vis=outs[f])
+            api.rbsm_rpcf(maps[f], xyz[f][0], xyz[f][1], xyz[f][2], k=k, vis=outs[f], workspace=ws)
 
     def rsmss():
         for f in range(frames):
@@ -655,9 +656,10 @@ def measure_rpcf(api, maps, xyz, frames, n_frag, args, stream, k=3):
     for kk in (1, 5, 7):
         def rpcf_k(kk=kk):
             for f in range(few):
-                api.rbsm_rpcf(maps[f], xyz[f][0], xyz[f][1], xyz[f][2], k=kk, vis=outs[f])
+                api.rbsm_rpcf(maps[f], xyz[f][0], xyz[f][1], xyz[f][2], k=kk, vis=outs[f], workspace=ws)
         by_k[str(kk)] = few * n_frag / (timed(rpcf_k) * 1e-3) / 1e9
-    return {"metric": "Gfragments/s RPCF visibility (k x k PCF over RSMSS), same frames, one launch per frame",
+    return {"metric": "Gfragments/s RPCF visibility (k x k PCF over RSMSS), same frames, one launch per frame "
+                      "(rbsm_rpcf_ws)",
             "k": k, "value": fps(ms), "ms_per_step": ms, "launches_per_step": frames,
             "rsmss_same_launches": {"value": fps(ms_rsmss), "ms_per_step": ms_rsmss},
             "samples_per_fragment": k * k,

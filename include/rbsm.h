@@ -219,6 +219,20 @@ int rbsm_rpcf(const rbsm_map *map, const rbsm_frags *frags, float *vis, int32_t 
               const rbsm_params *params, void *stream);
 
 /*
+ * rbsm_rpcf with an 8-byte device workspace (8-byte aligned, owned by the
+ * caller, used by one call at a time: calls that overlap on the GPU need
+ * workspaces of their own).  The answers are those of rbsm_rpcf bit for
+ * bit.  For k > 1 the call first zeroes the workspace on `stream`, and the
+ * warps then take the tiles after their first one from that counter, one
+ * tile per claim, instead of a fixed partition, so that warps whose tiles
+ * carry many edge samples do not hold up the end of the launch.  For k = 1
+ * the workspace is not used.  Errors as for rbsm_rpcf, and RBSM_ERR_ARG
+ * for a NULL or unaligned workspace or one that overlaps vis or an input.
+ */
+int rbsm_rpcf_ws(const rbsm_map *map, const rbsm_frags *frags, float *vis, int32_t k,
+                 const rbsm_params *params, void *workspace, void *stream);
+
+/*
  * Batched evaluation: many shadow maps (lights, cascades) against many
  * fragment sets (views) in ONE persistent kernel launch.  Not in the paper,
  * which evaluates one map per shader pass; every job's answers are

@@ -124,6 +124,8 @@ def _declare(lib):
         f.argtypes = [_P(rbsm_map), _P(rbsm_frags), vp, vp, _P(rbsm_params), vp]
     lib.rbsm_rpcf.restype = i32
     lib.rbsm_rpcf.argtypes = [_P(rbsm_map), _P(rbsm_frags), vp, ctypes.c_int32, _P(rbsm_params), vp]
+    lib.rbsm_rpcf_ws.restype = i32
+    lib.rbsm_rpcf_ws.argtypes = [_P(rbsm_map), _P(rbsm_frags), vp, ctypes.c_int32, _P(rbsm_params), vp, vp]
     lib.rbsm_shadow_map.restype = i32
     lib.rbsm_shadow_map.argtypes = [_P(rbsm_occluders), vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, vp]
     lib.rbsm_shadow_maps.restype = i32

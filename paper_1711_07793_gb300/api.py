@@ -139,10 +139,12 @@ def rsmss_filter(depth, x, y, z, vis=None, codes=False, max_dist=N.RBSM_MAXDIST_
     """Revectorization-based shadow filtering (Listing 5): returns (vis, codes or None)."""
     return _single(N.lib().rsmss_filter, "rsmss_filter", depth, x, y, z, vis, codes, max_dist, stream)
 
-def rbsm_rpcf(depth, x, y, z, k=3, vis=None, max_dist=N.RBSM_MAXDIST_DEFAULT, stream=None):
+def rbsm_rpcf(depth, x, y, z, k=3, vis=None, max_dist=N.RBSM_MAXDIST_DEFAULT, stream=None, workspace=None):
     """RPCF (rbsm_rpcf): the mean RSMSS answer of the k x k samples shifted
     by whole texels around each fragment (PCF over Listing 5, §5.3).
-    CUDA tensors (or a MapTexture); returns vis."""
+    CUDA tensors (or a MapTexture); returns vis.  With `workspace` (a CUDA
+    tensor of at least 8 bytes, used by one call at a time) the call is
+    rbsm_rpcf_ws: the same answers, tiles taken from a counter."""
     m = map_desc(depth)
     f = frags_desc(x, y, z)
     if vis is None:
@@ -150,8 +152,17 @@ def rbsm_rpcf(depth, x, y, z, k=3, vis=None, max_dist=N.RBSM_MAXDIST_DEFAULT, st
     else:
         _check_plane("vis", vis, f.n)
     p = _params(max_dist)
-    N.check("rbsm_rpcf", N.lib().rbsm_rpcf(ctypes.byref(m), ctypes.byref(f), ctypes.c_void_p(vis.data_ptr()),
-                                           int(k), ctypes.byref(p), _stream_handle(stream)))
+    if workspace is None:
+        N.check("rbsm_rpcf", N.lib().rbsm_rpcf(ctypes.byref(m), ctypes.byref(f), ctypes.c_void_p(vis.data_ptr()),
+                                               int(k), ctypes.byref(p), _stream_handle(stream)))
+    else:
+        if not isinstance(workspace, torch.Tensor) or not workspace.is_cuda or \
+                workspace.numel() * workspace.element_size() < 8:
+            raise TypeError("workspace must be a CUDA tensor of at least 8 bytes")
+        N.check("rbsm_rpcf_ws", N.lib().rbsm_rpcf_ws(ctypes.byref(m), ctypes.byref(f),
+                                                     ctypes.c_void_p(vis.data_ptr()), int(k), ctypes.byref(p),
+                                                     ctypes.c_void_p(workspace.data_ptr()),
+                                                     _stream_handle(stream)))
     return vis
 
 

@@ -174,7 +174,8 @@ __device__ __forceinline__ void block_bits(const MapDev &m, float u, float v, fl
 template <int K, int kThreads>
 __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
 rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict__ y,
-            const float *__restrict__ z, long long n, float *__restrict__ vis, int max_dist, bool vec_planes)
+            const float *__restrict__ z, long long n, float *__restrict__ vis, int max_dist, bool vec_planes,
+            unsigned long long *next_tile)
 {
     constexpr int kWarps = kThreads / 32;
     constexpr int R = (K - 1) / 2;
@@ -188,6 +189,14 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
     long long tile = (long long)blockIdx.x * kWarps + warp;
     if (tile >= tiles)
         return;
+    // schedule: every warp takes one tile of the first wave; after that
+    // either the static stride or, with a counter (next_tile, k > 1), one
+    // tile per claim, taken one tile ahead, so that warps whose tiles carry
+    // many edge samples do not hold up the end of the launch
+    const bool claims = K > 1 && next_tile != nullptr;
+    unsigned long long claim = 0;
+    if (claims && lane == 0)
+        claim = atomicAdd(next_tile, 1ull);
     const float W = (float)m.width, H = (float)m.height;
     // the largest floor(u), floor(v) whose block lies inside the map
     const float uhi = (float)(m.width - R - 2), vhi = (float)(m.height - R - 2);
@@ -254,7 +263,12 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
     stage_tile(t, lane, buf);
     int queued = 0;
     for (;;) {
-        const long long nt = tile + stride;
+        long long nt = tile + stride;
+        if (claims) {
+            nt = stride + (long long)__shfl_sync(0xffffffffu, claim, 0);
+            if (nt < tiles && lane == 0)
+                claim = atomicAdd(next_tile, 1ull);
+        }
         const bool more = nt < tiles;
         WarpTileIO tn;
         LaneCoords c;
@@ -395,7 +409,8 @@ rpcf_kernel(const MapDev m, const float *__restrict__ x, const float *__restrict
 }
 
 template <int K>
-int launch_rpcf(const rbsm_map &map, const rbsm_frags &f, float *vis, int max_dist, cudaStream_t stream)
+int launch_rpcf(const rbsm_map &map, const rbsm_frags &f, float *vis, int max_dist, unsigned long long *ctr,
+                cudaStream_t stream)
 {
     auto kern = rpcf_kernel<K, kRpcfThreads>;
     static KernelSetup setup;
@@ -412,7 +427,13 @@ int launch_rpcf(const rbsm_map &map, const rbsm_frags &f, float *vis, int max_di
     if (grid > blocks_needed)
         grid = blocks_needed;
     const bool vec = aligned16(f.x) && aligned16(f.y) && aligned16(f.z);
-    kern<<<(unsigned)grid, kRpcfThreads, 0, stream>>>(to_dev(map), f.x, f.y, f.z, f.n, vis, max_dist, vec);
+    if (K > 1 && ctr) {
+        const cudaError_t ez = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), stream);
+        if (ez != cudaSuccess)
+            return cuda_fail(ez);
+    }
+    kern<<<(unsigned)grid, kRpcfThreads, 0, stream>>>(to_dev(map), f.x, f.y, f.z, f.n, vis, max_dist, vec,
+                                                      K > 1 ? ctr : nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return cuda_fail(e);
@@ -422,10 +443,12 @@ int launch_rpcf(const rbsm_map &map, const rbsm_frags &f, float *vis, int max_di
 }  // namespace
 }  // namespace rbsm
 
-extern "C" int rbsm_rpcf(const rbsm_map *map, const rbsm_frags *frags, float *vis, int32_t k,
-                         const rbsm_params *params, void *stream)
+namespace rbsm {
+namespace {
+
+int rpcf_entry(const rbsm_map *map, const rbsm_frags *frags, float *vis, int32_t k, const rbsm_params *params,
+               unsigned long long *ctr, void *stream)
 {
-    using namespace rbsm;
     int rc, max_dist;
     if ((rc = check_map(map)) != RBSM_OK) return rc;
     if ((rc = check_frags(frags)) != RBSM_OK) return rc;
@@ -441,11 +464,32 @@ extern "C" int rbsm_rpcf(const rbsm_map *map, const rbsm_frags *frags, float *vi
     // vis holds partial sums while the kernel runs: it must not overlap an input
     if (overlaps_inputs(*map, *frags, vis, (size_t)frags->n * 4u))
         return RBSM_ERR_ARG;
+    if (ctr && (overlaps_inputs(*map, *frags, ctr, 8) ||
+                (reinterpret_cast<uintptr_t>(ctr) < reinterpret_cast<uintptr_t>(vis) + (uintptr_t)frags->n * 4u &&
+                 reinterpret_cast<uintptr_t>(vis) < reinterpret_cast<uintptr_t>(ctr) + 8u)))
+        return RBSM_ERR_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     switch (k) {
-    case 1: return launch_rpcf<1>(*map, *frags, vis, max_dist, s);
-    case 3: return launch_rpcf<3>(*map, *frags, vis, max_dist, s);
-    case 5: return launch_rpcf<5>(*map, *frags, vis, max_dist, s);
-    default: return launch_rpcf<7>(*map, *frags, vis, max_dist, s);
+    case 1: return launch_rpcf<1>(*map, *frags, vis, max_dist, ctr, s);
+    case 3: return launch_rpcf<3>(*map, *frags, vis, max_dist, ctr, s);
+    case 5: return launch_rpcf<5>(*map, *frags, vis, max_dist, ctr, s);
+    default: return launch_rpcf<7>(*map, *frags, vis, max_dist, ctr, s);
     }
+}
+
+}  // namespace
+}  // namespace rbsm
+
+extern "C" int rbsm_rpcf(const rbsm_map *map, const rbsm_frags *frags, float *vis, int32_t k,
+                         const rbsm_params *params, void *stream)
+{
+    return rbsm::rpcf_entry(map, frags, vis, k, params, nullptr, stream);
+}
+
+extern "C" int rbsm_rpcf_ws(const rbsm_map *map, const rbsm_frags *frags, float *vis, int32_t k,
+                            const rbsm_params *params, void *workspace, void *stream)
+{
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 7u) != 0)
+        return RBSM_ERR_ARG;
+    return rbsm::rpcf_entry(map, frags, vis, k, params, reinterpret_cast<unsigned long long *>(workspace), stream);
 }

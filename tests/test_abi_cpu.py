@@ -144,8 +144,16 @@ def test_bad_arguments_are_rejected_before_any_cuda_call(native):
     sep_frags = N.rbsm_frags(pa, pa + 64, pa + 128, 16)
     for vis_at in (pa, pa + 96, pa + 188, addr + 60):       # over x, y, z, the map
         assert lib.rbsm_rpcf(B(good_map), B(sep_frags), vis_at, 3, B(p), None) == N.RBSM_ERR_ARG
+        assert lib.rbsm_rpcf_ws(B(good_map), B(sep_frags), vis_at, 3, B(p), wa, None) == N.RBSM_ERR_ARG
         for fn in (lib.rbsm_visibility, lib.rsmss_filter):
             assert fn(B(good_map), B(sep_frags), vis_at, None, B(p), None) == N.RBSM_ERR_ARG
+    vis_buf = (ctypes.c_float * 32)()
+    va = ctypes.addressof(vis_buf)
+    assert lib.rbsm_rpcf_ws(B(good_map), B(sep_frags), va, 3, B(p), None, None) == N.RBSM_ERR_ARG   # no workspace
+    assert lib.rbsm_rpcf_ws(B(good_map), B(sep_frags), va, 3, B(p), wa + 4, None) == N.RBSM_ERR_ARG  # unaligned
+    assert lib.rbsm_rpcf_ws(B(good_map), B(sep_frags), va, 3, B(p), va + 8, None) == N.RBSM_ERR_ARG  # inside vis
+    assert lib.rbsm_rpcf_ws(B(good_map), B(sep_frags), va, 3, B(p), pa + 8, None) == N.RBSM_ERR_ARG  # inside x
+    assert lib.rbsm_rpcf_ws(B(good_map), B(sep_frags), va, 2, B(p), wa, None) == N.RBSM_ERR_ARG      # even k
     codes_buf = (ctypes.c_uint16 * 64)()
     for fn in (lib.rbsm_visibility, lib.rsmss_filter):             # codes over z
         assert fn(B(good_map), B(sep_frags), ctypes.addressof(codes_buf), pa + 150, B(p), None) == N.RBSM_ERR_ARG

@@ -195,3 +195,27 @@ def test_shared_block_at_the_maximum_extent(api, k):
     y = (rng.uniform(0, h, uu.size) / h).astype(np.float32)
     z = np.full_like(x, 0.5)
     check(api, depth, x, y, z, k, "max extent k=%d" % k)
+
+
+@pytest.mark.parametrize("k", [1, 3, 5, 7])
+def test_workspace_schedule_gives_the_same_bits(api, k):
+    """rbsm_rpcf_ws (tiles taken from a counter) against rbsm_rpcf (a fixed
+    partition): the same bits on C2 at a reduced view, on odd maps with
+    borders and non-finite coordinates, and twice in a row with one
+    workspace (the call zeroes its counter)."""
+    import rbsm_scenes as sc
+    f = sc.config2(5, screen=(960, 540))
+    rng = np.random.default_rng(40 + k)
+    odd = np.where(rng.random((129, 257)) < 0.35, np.float32(0.25), np.float32(1.0)).astype(np.float32)
+    ox = rng.uniform(-0.3, 1.3, 30000).astype(np.float32)
+    oy = rng.uniform(-0.3, 1.3, 30000).astype(np.float32)
+    ox[::97] = np.nan
+    cases = [(f.depth, f.x, f.y, f.z), (odd, ox, oy, np.full_like(ox, 0.5))]
+    ws = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for depth, x, y, z in cases:
+        d, xs, ys, zs = dev(depth), dev(x), dev(y), dev(z)
+        ref = api.rbsm_rpcf(d, xs, ys, zs, k=k)
+        for _ in range(2):
+            got = api.rbsm_rpcf(d, xs, ys, zs, k=k, workspace=ws)
+            torch.cuda.synchronize()
+            assert torch.equal(got.view(torch.int32), ref.view(torch.int32))
