@@ -139,12 +139,28 @@ def rsmss_filter(depth, x, y, z, vis=None, codes=False, max_dist=N.RBSM_MAXDIST_
     """Revectorization-based shadow filtering (Listing 5): returns (vis, codes or None)."""
     return _single(N.lib().rsmss_filter, "rsmss_filter", depth, x, y, z, vis, codes, max_dist, stream)
 
-def rbsm_rpcf(depth, x, y, z, k=3, vis=None, max_dist=N.RBSM_MAXDIST_DEFAULT, stream=None, workspace=None):
-    """RPCF (rbsm_rpcf): the mean RSMSS answer of the k x k samples shifted
-    by whole texels around each fragment (PCF over Listing 5, §5.3).
-    CUDA tensors (or a MapTexture); returns vis.  With `workspace` (a CUDA
-    tensor of at least 8 bytes, used by one call at a time) the call is
-    rbsm_rpcf_ws: the same answers, tiles taken from a counter."""
+_RPCF_WORKSPACES = {}
+
+
+def _rpcf_workspace(device, stream):
+    """The 8-byte counter of rbsm_rpcf_ws kept per (device, stream): calls on
+    one stream run in order, so they can share it."""
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    key = (device.index, s.cuda_stream)
+    ws = _RPCF_WORKSPACES.get(key)
+    if ws is None:
+        ws = torch.zeros(1, dtype=torch.int64, device=device)
+        _RPCF_WORKSPACES[key] = ws
+    return ws
+
+
+def rbsm_rpcf(depth, x, y, z, k=3, vis=None, max_dist=N.RBSM_MAXDIST_DEFAULT, stream=None, workspace="auto"):
+    """RPCF: the mean RSMSS answer of the k x k samples shifted by whole
+    texels around each fragment (PCF over Listing 5, §5.3).  CUDA tensors
+    (or a MapTexture); returns vis.  workspace: "auto" (default) calls
+    rbsm_rpcf_ws with a counter kept per stream; a CUDA tensor of at least 8
+    bytes calls rbsm_rpcf_ws with that counter; None calls rbsm_rpcf (a
+    fixed partition of the tiles).  The answers are the same bits."""
     m = map_desc(depth)
     f = frags_desc(x, y, z)
     if vis is None:
@@ -152,6 +168,10 @@ def rbsm_rpcf(depth, x, y, z, k=3, vis=None, max_dist=N.RBSM_MAXDIST_DEFAULT, st
     else:
         _check_plane("vis", vis, f.n)
     p = _params(max_dist)
+    if isinstance(workspace, str):
+        if workspace != "auto":
+            raise ValueError("workspace must be 'auto', None or a CUDA tensor")
+        workspace = _rpcf_workspace(x.device, stream)
     if workspace is None:
         N.check("rbsm_rpcf", N.lib().rbsm_rpcf(ctypes.byref(m), ctypes.byref(f), ctypes.c_void_p(vis.data_ptr()),
                                                int(k), ctypes.byref(p), _stream_handle(stream)))

@@ -214,8 +214,10 @@ def test_workspace_schedule_gives_the_same_bits(api, k):
     ws = torch.zeros(1, dtype=torch.int64, device="cuda")
     for depth, x, y, z in cases:
         d, xs, ys, zs = dev(depth), dev(x), dev(y), dev(z)
-        ref = api.rbsm_rpcf(d, xs, ys, zs, k=k)
+        ref = api.rbsm_rpcf(d, xs, ys, zs, k=k, workspace=None)           # rbsm_rpcf
         for _ in range(2):
             got = api.rbsm_rpcf(d, xs, ys, zs, k=k, workspace=ws)
+            auto = api.rbsm_rpcf(d, xs, ys, zs, k=k)                     # the binding's per-stream counter
             torch.cuda.synchronize()
             assert torch.equal(got.view(torch.int32), ref.view(torch.int32))
+            assert torch.equal(auto.view(torch.int32), ref.view(torch.int32))
