@@ -9,15 +9,18 @@
 // gathers or five loads each); off-edge samples add their shadow test at
 // once, edge samples go to the warp's queue (fragment and sample index; for
 // k = 3 with the fragment's shadow tests, else the drain classifies the
-// sample again) and are walked 32 at a time on full warps.  For k > 1 a fragment with edge samples keeps its sum in the
-// output plane as a fixed-point integer (each sample answer rounded to
-// 2^-F, F = 24 / 22 / 20 for k = 3 / 5 / 7) below a count of its samples
-// still to come; the adds commute, so the result does not depend on their
-// order, and the add that takes the count to zero writes the mean in place.
-// A fragment without edge samples writes its mean at once, and one outside
-// the shared block (below) walks its own samples, so no second pass is
-// needed.  For k = 1 there is nothing to add and the answers are stored as
-// floats (rsmss_filter's bits).
+// sample again) and are walked 32 at a time on full warps.  For k > 1 a
+// fragment with edge samples keeps its sum in the output plane as a
+// fixed-point integer (each sample answer rounded to 2^-F, F = 24 / 22 / 20
+// for k = 3 / 5 / 7) below a count of its samples still to come; the adds
+// commute, so the result does not depend on their order, and the add that
+// takes the count to zero writes the mean in place.  A fragment without
+// edge samples writes its mean at once, and one outside the shared block
+// (below) walks its own samples, so no second pass is needed.  For k = 1
+// there is nothing to add and the answers are stored as floats
+// (rsmss_filter's bits).  Because the answers do not depend on the order of
+// the work, rbsm_rpcf_ws can hand the tiles out from a counter (balance
+// between warps) and give the same bits as rbsm_rpcf's fixed partition.
 #include <cuda_runtime.h>
 
 #include <cstdint>
